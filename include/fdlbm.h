@@ -1,0 +1,187 @@
+/*
+ * fdlbm.h -- C ABI of the GB300-native finite-difference lattice Boltzmann
+ * solver for compressible flow with high Mach number (Gan, Xu, Zhang, Yu, Li,
+ * arXiv 0801.4169).
+ *
+ * One handle is one 2-D solve on one GPU: a distribution f_ki(x, y) over the
+ * Watari-Tsutahara 33-velocity set (Sec. 2, Eq. 1; speeds v_1..v_4 =
+ * 1, 1.92, 2.99, 4.49 as in Sec. 4) on an nx x ny node grid with a ghost ring of
+ * width 2. Each step applies, at every node, the moments of Eqs. 3-5, the
+ * equilibrium of Eqs. 10-13, and the modified Lax-Wendroff update with
+ * dispersion and pressure-switched artificial viscosity of Eqs. 15-17 (the
+ * alpha = x, y terms summed, relaxation counted once), followed by the
+ * boundary fill of the ghost ring.
+ *
+ * Conventions for every call:
+ *  - All physical arguments and results are FP64, whatever the storage
+ *    precision. Macroscopic arrays hold nx*ny values, x fastest
+ *    (index j*nx + i for node i along x, j along y). rho = n (m = 1),
+ *    u, v are the x/y velocity, T the temperature (theta = T), p = rho*T.
+ *  - Host pointers are owned by the caller and are not retained after the call
+ *    returns. "_device" variants take device pointers that must stay valid
+ *    until the handle's stream has passed the call.
+ *  - Every call returns FDLBM_OK (0) or a negative fdlbm_status.
+ *    fdlbm_last_error(h) then describes the failure.
+ *  - Errors are sticky. After FDLBM_E_NUMERIC or FDLBM_E_CUDA, fdlbm_step
+ *    refuses to run. fdlbm_get_macro, fdlbm_save and fdlbm_destroy still work,
+ *    and fdlbm_set_macro / fdlbm_load clear the error.
+ *  - A handle is not thread safe; different handles may be used from
+ *    different threads.
+ *
+ * Numerical readings of points the paper leaves open:
+ *  - Eq. 10: all five bracket terms sit inside nF_k[...].
+ *  - gamma = 2 (2-D, e_int = nT).
+ *  - Moments are taken of f.
+ *  - The scheme is explicit at time t.
+ *  - Boundary mechanics, which the paper does not give, are set out at
+ *    enum fdlbm_bc.
+ */
+#ifndef FDLBM_H
+#define FDLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdlbm_ctx* fdlbm_t;
+
+enum fdlbm_status {
+  FDLBM_OK = 0,
+  FDLBM_E_ARG = -1,     /* invalid argument (sizes, kinds, NULL pointers, wrong handle state) */
+  FDLBM_E_OOM = -2,     /* device or pinned-host allocation failed, or caller memory too small */
+  FDLBM_E_CUDA = -3,    /* a CUDA runtime call failed; message in fdlbm_last_error */
+  FDLBM_E_NUMERIC = -4, /* a node had non-finite moments, n <= 0 or T <= 0 (P <= 0, Eq. 16 undefined) */
+  FDLBM_E_TIMEOUT = -5, /* a bounded device or host wait gave up */
+  FDLBM_E_STATE = -6,   /* call not valid in the handle's state (e.g. step before set_macro) */
+  FDLBM_E_IO = -7       /* checkpoint file could not be written/read or does not match the handle */
+};
+
+/* Boundary kinds per side (Sec. 5.2 names reflecting, supersonic-outflow and
+ * Dirichlet boundaries; the paper gives no mechanics). Ghost ring of width 2:
+ *  PERIODIC  ghost node g copies interior node g mod n (both sides of an axis must be periodic);
+ *  OUTFLOW   zero gradient: both ghost layers copy the nearest interior node;
+ *  DIRICHLET ghosts hold f_eq of the state given by fdlbm_set_boundary_state (default rho=1,u=v=0,T=1);
+ *  WALL      specular reflection: ghost node -1-j mirrors node j with the normal
+ *            velocity component reversed (needs n >= 2 along that axis). */
+enum fdlbm_bc { FDLBM_BC_PERIODIC = 0, FDLBM_BC_OUTFLOW = 1, FDLBM_BC_DIRICHLET = 2, FDLBM_BC_WALL = 3 };
+
+enum fdlbm_side { FDLBM_LEFT = 0, FDLBM_RIGHT = 1, FDLBM_BOTTOM = 2, FDLBM_TOP = 3 };
+
+/* Storage / arithmetic precision.
+ *  FP64        f stored in FP64; moments, f_eq and the stencil in FP64.
+ *  FP32_STORE  f stored and differenced in FP32; moments (Eqs. 3-5), weights and
+ *              f_eq (Eqs. 10-13) evaluated in FP64. */
+enum fdlbm_prec { FDLBM_FP64 = 0, FDLBM_FP32_STORE = 1 };
+
+/* Scheme variants of Sec. 4 (Fig. 2, Fig. 3): drop line II, III or IV of Eq. 17,
+ * or hold the switch theta_alphaI of Eq. 16 at lambda. Default 0 = full Eq. 17. */
+enum fdlbm_flags {
+  FDLBM_NO_LW = 1,
+  FDLBM_NO_DISP = 2,
+  FDLBM_NO_VISC = 4,
+  FDLBM_SWITCH_CONST = 8
+};
+
+/* Health bits reported by fdlbm_health. */
+enum fdlbm_health_bits {
+  FDLBM_HEALTH_NUMERIC = 1, /* non-finite moment, n <= 0 or T <= 0 seen (=> FDLBM_E_NUMERIC) */
+  FDLBM_HEALTH_KAPPA = 2    /* |kappa_alpha| = |u_alpha| dt/dr_alpha > 1 seen (Eq. 15); informational */
+};
+
+/* Problem description (Eqs. 15-17 parameters). dx, dy, dt, tau > 0; lambda >= 0. */
+typedef struct {
+  int nx, ny;          /* interior nodes, >= 1 each */
+  double dx, dy;       /* mesh spacing Delta r_alpha */
+  double dt;           /* time step Delta t */
+  double tau;          /* BGK relaxation time (Eq. 2) */
+  double lambda;       /* artificial-viscosity amplitude (Eq. 16) */
+  int bc[4];           /* enum fdlbm_bc for left, right, bottom, top */
+  int prec;            /* enum fdlbm_prec */
+  int flags;           /* enum fdlbm_flags */
+} fdlbm_config;
+
+/* Device bytes a handle needs for cfg (two f buffers, staging for the macro
+ * arrays of the host-pointer calls, and a health word). 0 if cfg is invalid. */
+size_t fdlbm_device_bytes(const fdlbm_config* cfg);
+
+/* Create a solve. device_mem: NULL to let the library cudaMalloc, or caller
+ * device memory of at least fdlbm_device_bytes(cfg) bytes, 256-byte aligned,
+ * that outlives the handle (e.g. a PyTorch tensor). cuda_stream: a
+ * cudaStream_t, or NULL for the legacy default stream; all device work of the
+ * handle is ordered on it. The state is undefined until fdlbm_set_macro. */
+int fdlbm_create_ex(fdlbm_t* out, const fdlbm_config* cfg, void* device_mem, size_t device_bytes,
+                    void* cuda_stream);
+
+/* Convenience form of fdlbm_create_ex with flags = 0 and library-owned memory. */
+int fdlbm_create(fdlbm_t* out, int nx, int ny, double dx, double dy, double dt, double tau,
+                 double lambda, const int bc[4], int prec, void* cuda_stream);
+
+/* Prescribed state (rho, u, v, T) of a DIRICHLET side (enum fdlbm_side); its
+ * ghosts become f_eq of that state (Eq. 10). Enqueued on the stream. */
+int fdlbm_set_boundary_state(fdlbm_t h, int side, double rho, double u, double v, double T);
+
+/* Initial condition: f = f_eq(rho, u, v, T) at every node (Eq. 10), ghost ring
+ * filled per boundary kind. Host arrays of nx*ny doubles; copied before
+ * return. Resets the step count and clears a sticky error. */
+int fdlbm_set_macro(fdlbm_t h, const double* rho, const double* u, const double* v, const double* T);
+
+/* As fdlbm_set_macro with device arrays; asynchronous on the handle's stream. */
+int fdlbm_set_macro_device(fdlbm_t h, const double* rho, const double* u, const double* v,
+                           const double* T);
+
+/* Advance nsteps >= 0 time steps (Eq. 17), asynchronously on the stream.
+ * Returns a sticky error found by an earlier step, else FDLBM_OK; numerical
+ * failure inside these steps is reported by a later call (fdlbm_sync,
+ * fdlbm_get_macro, or the next fdlbm_step once the device has passed it). */
+int fdlbm_step(fdlbm_t h, long nsteps);
+
+/* Wait for the handle's stream and return its status (FDLBM_E_NUMERIC if a
+ * step saw a bad node). */
+int fdlbm_sync(fdlbm_t h);
+
+/* Moments (Eqs. 3-5) of the current f at every node into caller host arrays
+ * of nx*ny doubles. Synchronises the stream. Works after a sticky error (then
+ * it returns that error after filling the arrays). */
+int fdlbm_get_macro(fdlbm_t h, double* rho, double* u, double* v, double* T);
+
+/* As fdlbm_get_macro into device arrays; asynchronous, no status check. */
+int fdlbm_get_macro_device(fdlbm_t h, double* rho, double* u, double* v, double* T);
+
+/* Raw distribution of the interior, converted to FP64, layout [q][j][i]
+ * (33*nx*ny doubles, q = 0 rest, q = 1 + 8(k-1) + (i-1) for speed k and
+ * direction angle i*pi/4). Host arrays; synchronises. */
+int fdlbm_get_f(fdlbm_t h, double* f);
+
+/* Set the raw interior distribution (same layout; rounded to the storage
+ * precision) and refill the ghost ring. Host array; synchronises. */
+int fdlbm_set_f(fdlbm_t h, const double* f);
+
+/* Checkpoint: write / read the current f (storage precision, bit exact), the
+ * step count, the boundary states and the configuration to a file. fdlbm_load
+ * requires a handle with the same configuration and returns FDLBM_E_IO otherwise. */
+int fdlbm_save(fdlbm_t h, const char* path);
+int fdlbm_load(fdlbm_t h, const char* path);
+
+/* Steps taken since the last set_macro/load (+ the loaded count). */
+long fdlbm_steps_done(fdlbm_t h);
+
+/* Health bits (enum fdlbm_health_bits) accumulated since set_macro; synchronises. */
+unsigned fdlbm_health(fdlbm_t h);
+
+/* Release the handle and the memory it owns. NULL-safe. */
+int fdlbm_destroy(fdlbm_t h);
+
+/* Message describing the last failure on h, or, for h == NULL, the last
+ * failure of fdlbm_create* on the calling thread. Never NULL. */
+const char* fdlbm_last_error(fdlbm_t h);
+
+/* Library version string. */
+const char* fdlbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDLBM_H */
