@@ -1,0 +1,289 @@
+"""Benchmark of the fused FDLBM step on GB300 (one JSON line on rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec fp32|fp64] [--impl reference]
+
+A "step" is one time step of the whole method (moments -> f_eq -> Eq. 17 -> boundary fill) over
+the workload's grid. The metric is GLUPS: site updates of all 33 velocities per second (nx*ny*steps/s).
+
+Default workload: the 4096 x 4096 four-quadrant Riemann problem (FP32 f, FP64 moments and f_eq,
+dx = 2.5e-4, dt = tau = 2.5e-6, lambda = 1, outflow on every side). Its f pair is 4.4 GB, far
+above the 129 MB L2, so no L2 flush is needed between steps.
+
+- value: device time over K steps from CUDA events on the solver's stream, with inputs already
+  resident in HBM.
+- e2e: the public call sequence with pinned host buffers inside the timed region:
+  fdlbm_set_macro (H2D), fdlbm_step(K), fdlbm_get_macro (D2H).
+- roofline: the fused step kernel against the FP64 pipe. Each FP64 instruction, FP32<->FP64
+  conversions included, issues at ~1.6 per clock per SM on this part, so the kernel is bound by
+  FP64 issue, not HBM. The HBM figures are reported beside it.
+- cpu_baseline: the FP64 CPU oracle, timed on a bounded sample of the same workload.
+
+N > 1 (torchrun): every rank runs an independent replica with its own seed (weak scaling, no
+data-path collective); the time is the max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic FP64-pipe operations per site update of the fused step (counted op by op; the
+# breakdown is in the design notes). FP32<->FP64 conversions issue on the FP64 pipe too.
+FP64_OPS_PER_LUP = {"fp64": 627, "fp32": 324}
+# Minimum HBM bytes per site update: read and write all 33 f once.
+BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4}
+# FP64 issue rate measured on this machine's GB300 (DFMA microbenchmark: 1.6 per clock per SM).
+FP64_OPS_PER_CLK_SM = 1.6
+N_SM = 152
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def make_workload(name, seed=0, small=False, n=None):
+    from paper_0801_4169_gb300 import workloads as W
+    if name == "riemann4096":
+        return W.riemann4q(n=n or (256 if small else 4096), seed=seed)
+    if name == "reflection1200x300":
+        return W.reflection(nx=300, ny=75) if small else W.reflection()
+    if name == "shock4000x4":
+        return W.shock_tube(nx=400 if small else 4000)
+    if name == "sod400x4":
+        return W.sod()
+    raise SystemExit("unknown workload %s" % name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(name, budget_s=20.0):
+    """Time the FP64 CPU oracle on a bounded sample of the workload (a sub-grid, a few steps)."""
+    from oracle import fdlbm as O
+    from paper_0801_4169_gb300 import workloads as W
+    if name == "riemann4096":
+        w = W.riemann4q(n=256, seed=0)
+        sample = "256x256 sub-grid of the four-quadrant problem (same dx, dt, states)"
+    elif name == "reflection1200x300":
+        w = W.reflection(nx=300, ny=75)
+        sample = "300x75 downscale of the reflection problem"
+    elif name == "shock4000x4":
+        w = W.shock_tube(nx=4000, ny=1)
+        sample = "4000x1 (y-uniform rows are identical)"
+    else:
+        w = W.sod(ny=1)
+        sample = "400x1 (y-uniform rows are identical)"
+    s = O.Sim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, w.bstate)
+    s.set_macro(*w.macros())
+    s.step(1)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        rc = s.step(5)
+        steps += 5
+        if rc:
+            break
+    el = time.perf_counter() - t0
+    return {"value": w.nx * w.ny * steps / el / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%s, %d steps, %.1f s single-threaded FP64 C" % (sample, steps, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = oracle_sample(args.workload, budget_s=max(5.0, min(60.0, 4.0 * args.steps)))
+    line = {"impl": "reference", "metric": "GLUPS", "value": cb["value"], "unit": "GLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "impl": "FP64 CPU oracle (oracle/fdlbm_oracle.c)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="riemann4096",
+                    choices=["riemann4096", "reflection1200x300", "shock4000x4", "sod400x4"])
+    ap.add_argument("--prec", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="a small version of the workload (profiling)")
+    ap.add_argument("--n", type=int, default=None, help="grid edge of the four-quadrant workload (profiling)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_0801_4169_gb300 import fdlbm as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec_name = args.prec or ("fp64" if args.workload == "sod400x4" else "fp32")
+    prec = F.FDLBM_FP64 if prec_name == "fp64" else F.FDLBM_FP32_STORE
+
+    w = make_workload(args.workload, seed=rank, small=args.small, n=args.n)
+    stream = torch.cuda.Stream()
+    solver = F.Solver(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, prec, 0, w.bstate, stream=stream)
+    # pinned host copies of the inputs (for the end-to-end leg)
+    pinned = []
+    for a in w.macros():
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        pinned.append(t.numpy())
+    solver.set_macro(*pinned)
+    times = solver.autotune(3)
+    variant = F.fdlbm_get_variant(solver.h)
+    solver.step(args.warmup)
+    solver.sync()
+
+    sampler = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    status = solver.sync()
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.barrier()
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    lups = w.nx * w.ny * args.steps
+    glups = lups * world / (ms_max * 1e-3) / 1e9
+    per_launch_ms = ms / args.steps
+
+    # end-to-end: the public API with pinned host buffers, copies inside the timed region
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    h_out = [torch.empty(a.shape, dtype=torch.float64, pin_memory=True).numpy() for a in w.macros()]
+    t0 = time.perf_counter()
+    solver.set_macro(*pinned)
+    solver.step(args.steps)
+    rc = F.lib().fdlbm_get_macro(solver.h, *[F._hp(a) for a in h_out])
+    t_e2e = time.perf_counter() - t0
+    t_e2e_t = torch.tensor([t_e2e], device="cuda")
+    if dist:
+        dist.all_reduce(t_e2e_t, op=dist.ReduceOp.MAX)
+    e2e_glups = lups * world / float(t_e2e_t.item()) / 1e9
+    macro_bytes = 4 * w.nx * w.ny * 8
+
+    peaks, peak_kind = load_peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * sm_mhz * 1e6 / 1e9  # G ops/s at the sampled clock
+    site_rate = w.nx * w.ny / (per_launch_ms * 1e-3)
+    achieved = FP64_OPS_PER_LUP[prec_name] * site_rate / 1e9
+    hbm_gbs = BYTES_PER_LUP[prec_name] * site_rate / 1e9
+
+    line = {
+        "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if prec_name == "fp64" else "f32-store/f64-moments-feq",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "precision": prec_name,
+                   "tile_variant": variant, "autotune_ms": [round(t, 4) for t in times],
+                   "l2": "inputs larger than L2 (f pair %.2f GB)" % (2 * 33 * w.nx * w.ny * (8 if prec_name == "fp64" else 4) / 1e9)
+                   if w.nx * w.ny * 33 * 4 > 129e6 else "inputs smaller than L2: steps read a warm cache",
+                   "status": status, "parallelism": "replicas%d" % world},
+        "roofline": {"bound": "alu", "kernel": "k_step (fused step)", "achieved": achieved,
+                     "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak,
+                     "traffic": None, "peak_derivation": "1.6 FP64 ops/clk/SM (measured DFMA issue) x 152 SMs x %.0f MHz" % sm_mhz,
+                     "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"), "peak_kind": peak_kind,
+                             "frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0)}},
+        "clocks": clocks,
+        "e2e": {"value": e2e_glups, "unit": "GLUPS", "h2d_bytes_per_step": macro_bytes / args.steps,
+                "d2h_bytes_per_step": macro_bytes / args.steps, "status": int(rc),
+                "note": "one solve per timed region: set_macro (H2D) + %d steps + get_macro (D2H)" % args.steps},
+        "gpu_launches": args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(args.workload, budget_s=20.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,18 @@ int fdlbm_set_f(fdlbm_t h, const double* f);
 int fdlbm_save(fdlbm_t h, const char* path);
 int fdlbm_load(fdlbm_t h, const char* path);
 
+/* Launch variants of the fused step (CTA tile shapes). Every variant gives bitwise identical
+ * results: a node's arithmetic does not depend on the tiling. */
+int fdlbm_variant_count(void);
+int fdlbm_set_variant(fdlbm_t h, int variant);  /* FDLBM_E_ARG if out of range */
+int fdlbm_get_variant(fdlbm_t h);               /* current variant, or a negative status */
+
+/* Autotuner: time every variant with trial_steps launches on the current state and keep the
+ * fastest. The state is not advanced: each trial launch reads the current buffer and writes the
+ * other, which the next real step overwrites. times_ms (may be NULL) receives
+ * fdlbm_variant_count() mean launch times in milliseconds. Synchronises the stream. */
+int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms);
+
 /* Steps taken since the last set_macro/load (+ the loaded count). */
 long fdlbm_steps_done(fdlbm_t h);
 

@@ -1,0 +1,72 @@
+// fdlbm_internal.h -- types shared by the host (C ABI) and device (kernels) halves of the
+// CUDA library. Not part of the public ABI (include/fdlbm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdlbm {
+
+constexpr int Q = 33;   // Watari-Tsutahara velocity count: rest + 4 speeds x 8 directions (Eq. 1)
+constexpr int NG = 2;   // ghost ring width: Eq. 17 reaches I +- 2 along each axis
+
+// Scheme flags (same values as enum fdlbm_flags).
+constexpr int F_NO_LW = 1, F_NO_DISP = 2, F_NO_VISC = 4, F_SWITCH_CONST = 8;
+// Boundary kinds (same values as enum fdlbm_bc).
+constexpr int BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_DIRICHLET = 2, BC_WALL = 3;
+// Health bits (same values as enum fdlbm_health_bits).
+constexpr unsigned H_NUMERIC = 1u, H_KAPPA = 2u;
+
+// Layout of one distribution buffer: SoA planes f[q][row][col] with row = j + 2, col = i + 2
+// (ghost ring of width 2 stored in place), row pitch padded to 32 elements so every row starts
+// on a 128-byte (FP32) or 256-byte (FP64) boundary.
+struct Grid {
+  int nx, ny;
+  int pitch;        // elements per row, multiple of 32, >= nx + 4
+  int rows;         // ny + 4
+  long long plane;  // pitch * rows (elements per velocity plane)
+  int bc[4];        // left, right, bottom, top
+  int flags;
+};
+
+// Per-solve constants computed once on the host in FP64 and passed by value (kernel parameter
+// space), so every thread reads them as uniform operands.
+struct Coeffs {
+  // Eq. 11 in Horner form: F_k(th) = th*(h[k][0] + th*(h[k][1] + th*(h[k][2] + th*h[k][3]))).
+  double Fh[4][4];
+  double v[4];        // speeds v_1..v_4
+  double v2[4];       // v_k^2
+  double v3_6[4];     // v_k^3 / 6
+  double v4_24[4];    // v_k^4 / 24
+  // Eq. 17 stencil weights without line IV, for axis a (0 = x, 1 = y), ring k, class c (0 = the
+  // two axis-aligned directions, |c| = v_k dt/dr_a; 1 = the four diagonals, |c| = v_k dt/(sqrt2 dr_a)),
+  // for the direction with positive c. The negative direction swaps W1/Wm1 and negates D.
+  double W1[2][4][2];   // coefficient of f_{I+1}: -c/2 + c^2/2 - 2d
+  double Wm1[2][4][2];  // coefficient of f_{I-1}: +c/2 + c^2/2 + 2d
+  double D[2][4][2];    // coefficient of (f_{I+2} - f_{I-2}): d = c(1 - c^2)/12
+  double C2[4][3];      // centre weight of line II summed over alpha: class 0 = x-axis dirs,
+                        // 1 = y-axis dirs, 2 = diagonals
+  double r;             // dt / tau
+  double kx, ky;        // dt/dx, dt/dy  (kappa_alpha = u_alpha * k_alpha, Eq. 15)
+  double lam;           // lambda of Eq. 16
+  // FP32 copies used by the FP32-storage stencil
+  float fW1[2][4][2], fWm1[2][4][2], fD[2][4][2], fC2[4][3];
+  float fr;
+};
+
+// Launch configuration of the fused step (tile of TW x TH nodes per CTA).
+enum StepVariant { V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_COUNT = 5 };
+
+// Kernel launchers (fdlbm_step.cu). All return cudaGetLastError() of the launch.
+cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
+                        unsigned* health, cudaStream_t s);
+cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
+                        const double* v, const double* T, cudaStream_t s);
+cudaError_t launch_dirichlet(int prec, void* f, const Grid& g, const Coeffs& c, const double bstate[4][4],
+                             cudaStream_t s);
+cudaError_t launch_macro(int prec, const void* f, const Grid& g, double* rho, double* u, double* v, double* T,
+                         cudaStream_t s);
+cudaError_t launch_get_f(int prec, const void* f, const Grid& g, double* out, cudaStream_t s);
+cudaError_t launch_set_f(int prec, void* f, const Grid& g, const double* in, cudaStream_t s);
+
+}  // namespace fdlbm

@@ -1,0 +1,323 @@
+"""Thin ctypes binding of the C ABI in include/fdlbm.h (libfdlbm_gb300.so).
+
+Functions carry the C names and only marshal arguments: numpy arrays for host pointers,
+torch tensors (or raw integer addresses) for device pointers, torch streams for cudaStream_t.
+A negative status raises FdlbmError carrying the code and fdlbm_last_error(). Every step of
+the method runs in the library's CUDA kernels; there is no other path. If the library cannot
+be loaded the import of this module's functions fails loudly.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfdlbm_gb300.so")
+
+FDLBM_OK, FDLBM_E_ARG, FDLBM_E_OOM, FDLBM_E_CUDA, FDLBM_E_NUMERIC, FDLBM_E_TIMEOUT, FDLBM_E_STATE, FDLBM_E_IO = \
+    0, -1, -2, -3, -4, -5, -6, -7
+FDLBM_BC_PERIODIC, FDLBM_BC_OUTFLOW, FDLBM_BC_DIRICHLET, FDLBM_BC_WALL = 0, 1, 2, 3
+FDLBM_LEFT, FDLBM_RIGHT, FDLBM_BOTTOM, FDLBM_TOP = 0, 1, 2, 3
+FDLBM_FP64, FDLBM_FP32_STORE = 0, 1
+FDLBM_NO_LW, FDLBM_NO_DISP, FDLBM_NO_VISC, FDLBM_SWITCH_CONST = 1, 2, 4, 8
+FDLBM_HEALTH_NUMERIC, FDLBM_HEALTH_KAPPA = 1, 2
+Q = 33
+
+
+class FdlbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fdlbm error %d: %s" % (code, msg))
+        self.code = code
+
+
+class fdlbm_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dt", ctypes.c_double), ("tau", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("bc", ctypes.c_int * 4), ("prec", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+_lib = None
+_DP = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+
+
+def lib():
+    """Load libfdlbm_gb300.so (building it first if sources changed and nvcc is present)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH) or os.environ.get("FDLBM_AUTOBUILD", "1") == "1":
+            try:
+                from . import build as _b
+                _b.build()
+            except RuntimeError:
+                if not os.path.exists(LIB_PATH):
+                    raise
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libfdlbm_gb300.so is missing; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        cfgp = ctypes.POINTER(fdlbm_config)
+        sig = {
+            "fdlbm_device_bytes": (ctypes.c_size_t, [cfgp]),
+            "fdlbm_create_ex": (ctypes.c_int, [ctypes.POINTER(_VP), cfgp, _VP, ctypes.c_size_t, _VP]),
+            "fdlbm_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 +
+                             [ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
+            "fdlbm_set_boundary_state": (ctypes.c_int, [_VP, ctypes.c_int] + [ctypes.c_double] * 4),
+            "fdlbm_set_macro": (ctypes.c_int, [_VP, _DP, _DP, _DP, _DP]),
+            "fdlbm_set_macro_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+            "fdlbm_step": (ctypes.c_int, [_VP, ctypes.c_long]),
+            "fdlbm_sync": (ctypes.c_int, [_VP]),
+            "fdlbm_get_macro": (ctypes.c_int, [_VP, _DP, _DP, _DP, _DP]),
+            "fdlbm_get_macro_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+            "fdlbm_get_f": (ctypes.c_int, [_VP, _DP]),
+            "fdlbm_set_f": (ctypes.c_int, [_VP, _DP]),
+            "fdlbm_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+            "fdlbm_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+            "fdlbm_variant_count": (ctypes.c_int, []),
+            "fdlbm_set_variant": (ctypes.c_int, [_VP, ctypes.c_int]),
+            "fdlbm_get_variant": (ctypes.c_int, [_VP]),
+            "fdlbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
+            "fdlbm_steps_done": (ctypes.c_long, [_VP]),
+            "fdlbm_health": (ctypes.c_uint, [_VP]),
+            "fdlbm_destroy": (ctypes.c_int, [_VP]),
+            "fdlbm_last_error": (ctypes.c_char_p, [_VP]),
+            "fdlbm_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(h, rc):
+    if rc < 0:
+        raise FdlbmError(rc, fdlbm_last_error(h))
+    return rc
+
+
+def _hp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _host(a, n):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def _dptr(t):
+    """Device address of a torch tensor (or an int address)."""
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_config(nx, ny, dx, dy, dt, tau, lam, bc, prec=FDLBM_FP64, flags=0):
+    c = fdlbm_config()
+    c.nx, c.ny, c.dx, c.dy, c.dt, c.tau, c.lambda_ = int(nx), int(ny), dx, dy, dt, tau, lam
+    for i in range(4):
+        c.bc[i] = int(bc[i])
+    c.prec, c.flags = int(prec), int(flags)
+    return c
+
+
+def fdlbm_device_bytes(cfg):
+    return int(lib().fdlbm_device_bytes(ctypes.byref(cfg)))
+
+
+def fdlbm_create_ex(cfg, device_mem=None, device_bytes=0, stream=None):
+    h = _VP()
+    rc = lib().fdlbm_create_ex(ctypes.byref(h), ctypes.byref(cfg), None if device_mem is None else _dptr(device_mem),
+                               int(device_bytes), _stream_ptr(stream))
+    _check(None, rc)
+    return h.value
+
+
+def fdlbm_create(nx, ny, dx, dy, dt, tau, lam, bc, prec=FDLBM_FP64, stream=None):
+    h = _VP()
+    bc_arr = (ctypes.c_int * 4)(*[int(b) for b in bc])
+    rc = lib().fdlbm_create(ctypes.byref(h), int(nx), int(ny), dx, dy, dt, tau, lam, bc_arr, int(prec),
+                            _stream_ptr(stream))
+    _check(None, rc)
+    return h.value
+
+
+def fdlbm_set_boundary_state(h, side, rho, u, v, T):
+    return _check(h, lib().fdlbm_set_boundary_state(h, int(side), rho, u, v, T))
+
+
+def fdlbm_set_macro(h, rho, u, v, T, n=None):
+    n = n if n is not None else np.asarray(rho).size
+    arrs = [_host(a, n) for a in (rho, u, v, T)]
+    return _check(h, lib().fdlbm_set_macro(h, *[_hp(a) for a in arrs]))
+
+
+def fdlbm_set_macro_device(h, rho, u, v, T):
+    return _check(h, lib().fdlbm_set_macro_device(h, *[_dptr(a) for a in (rho, u, v, T)]))
+
+
+def fdlbm_step(h, nsteps):
+    return _check(h, lib().fdlbm_step(h, int(nsteps)))
+
+
+def fdlbm_sync(h):
+    return _check(h, lib().fdlbm_sync(h))
+
+
+def fdlbm_get_macro(h, nx, ny, check=True):
+    out = [np.empty((ny, nx)) for _ in range(4)]
+    rc = lib().fdlbm_get_macro(h, *[_hp(a) for a in out])
+    if check:
+        _check(h, rc)
+    return tuple(out)
+
+
+def fdlbm_get_macro_device(h, rho, u, v, T):
+    return _check(h, lib().fdlbm_get_macro_device(h, *[_dptr(a) for a in (rho, u, v, T)]))
+
+
+def fdlbm_get_f(h, nx, ny):
+    f = np.empty((Q, ny, nx))
+    _check(h, lib().fdlbm_get_f(h, _hp(f)))
+    return f
+
+
+def fdlbm_set_f(h, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return _check(h, lib().fdlbm_set_f(h, _hp(f)))
+
+
+def fdlbm_save(h, path):
+    return _check(h, lib().fdlbm_save(h, os.fsencode(path)))
+
+
+def fdlbm_load(h, path):
+    return _check(h, lib().fdlbm_load(h, os.fsencode(path)))
+
+
+def fdlbm_variant_count():
+    return int(lib().fdlbm_variant_count())
+
+
+def fdlbm_set_variant(h, variant):
+    return _check(h, lib().fdlbm_set_variant(h, int(variant)))
+
+
+def fdlbm_get_variant(h):
+    return _check(h, lib().fdlbm_get_variant(h))
+
+
+def fdlbm_autotune(h, trial_steps=5):
+    """Returns the per-variant mean launch times (ms); the handle keeps the fastest variant."""
+    n = fdlbm_variant_count()
+    times = (ctypes.c_float * n)()
+    _check(h, lib().fdlbm_autotune(h, int(trial_steps), times))
+    return list(times)
+
+
+def fdlbm_steps_done(h):
+    return int(lib().fdlbm_steps_done(h))
+
+
+def fdlbm_health(h):
+    return int(lib().fdlbm_health(h))
+
+
+def fdlbm_destroy(h):
+    return lib().fdlbm_destroy(h)
+
+
+def fdlbm_last_error(h):
+    s = lib().fdlbm_last_error(h)
+    return s.decode() if s else ""
+
+
+def fdlbm_version():
+    return lib().fdlbm_version().decode()
+
+
+class Solver:
+    """One solve: owns a handle whose device memory is a torch uint8 tensor on the given stream."""
+
+    def __init__(self, nx, ny, dx, dy, dt, tau, lam, bc, prec=FDLBM_FP64, flags=0, bstate=None, stream=None,
+                 use_torch_memory=True):
+        self.nx, self.ny = int(nx), int(ny)
+        self.cfg = make_config(nx, ny, dx, dy, dt, tau, lam, bc, prec, flags)
+        self._mem = None
+        nbytes = fdlbm_device_bytes(self.cfg)
+        if nbytes == 0:
+            raise FdlbmError(FDLBM_E_ARG, "invalid configuration")
+        if use_torch_memory:
+            import torch
+            self._mem = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._mem.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            self.h = fdlbm_create_ex(self.cfg, aligned, nbytes, stream)
+        else:
+            self.h = fdlbm_create_ex(self.cfg, None, 0, stream)
+        if bstate is not None:
+            for side in range(4):
+                if int(bc[side]) == FDLBM_BC_DIRICHLET:
+                    fdlbm_set_boundary_state(self.h, side, *[float(x) for x in bstate[side]])
+
+    @classmethod
+    def from_workload(cls, w, prec=FDLBM_FP64, flags=0, stream=None, use_torch_memory=True):
+        s = cls(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, prec, flags, w.bstate, stream, use_torch_memory)
+        s.set_macro(*w.macros())
+        return s
+
+    def set_macro(self, rho, u, v, T):
+        n = self.nx * self.ny
+        return fdlbm_set_macro(self.h, rho, u, v, T, n)
+
+    def step(self, n):
+        return fdlbm_step(self.h, n)
+
+    def sync(self):
+        return fdlbm_sync(self.h)
+
+    def get_macro(self, check=True):
+        return fdlbm_get_macro(self.h, self.nx, self.ny, check)
+
+    def get_f(self):
+        return fdlbm_get_f(self.h, self.nx, self.ny)
+
+    def set_f(self, f):
+        return fdlbm_set_f(self.h, f)
+
+    def set_variant(self, v):
+        return fdlbm_set_variant(self.h, v)
+
+    def autotune(self, trial_steps=5):
+        return fdlbm_autotune(self.h, trial_steps)
+
+    @property
+    def steps_done(self):
+        return fdlbm_steps_done(self.h)
+
+    def health(self):
+        return fdlbm_health(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fdlbm_destroy(self.h)
+            self.h = None
+        self._mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

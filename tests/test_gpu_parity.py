@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle, element by element.
+
+Tolerances:
+- FP64 path: 1e-11 max relative error in rho, u, v, T after 1000 steps on the Sod tube. "Relative"
+  is to max(1, max|field|), since u and v can vanish.
+- f-level comparisons on small grids with every boundary kind and ragged tiles: 1e-12 relative to
+  max|f|. The two sides differ only in summation order and FMA contraction.
+- FP32-storage path: its error against the FP64 oracle is stated per case (storage rounding,
+  about kappa * 2^-24 per step).
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import fdlbm as O  # noqa: E402
+from paper_0801_4169_gb300 import fdlbm as F  # noqa: E402
+from paper_0801_4169_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    F.lib()
+
+
+def _smooth(nx, ny, seed, amp=0.1, base=(1.0, 0.3, -0.2, 1.0)):
+    rng = np.random.default_rng(seed)
+    x = 2 * np.pi * (np.arange(nx) + 0.5) / nx
+    y = 2 * np.pi * (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y)
+    out = []
+    for b in base:
+        a1, a2, p1, p2 = rng.uniform(-1, 1, 4)
+        out.append(b + amp * (abs(b) + 0.5) * (a1 * np.sin(X + p1) + a2 * np.cos(Y + 2 * X + p2)))
+    return out
+
+
+def _rel(got, ref):
+    return np.max(np.abs(got - ref)) / max(1.0, np.max(np.abs(ref)))
+
+
+def test_fp64_sod_1000_steps_matches_oracle():
+    """Sod tube, 400 x 4, 1000 steps, FP64: <= 1e-11 in rho, u, v, T; rows stay bitwise equal."""
+    w = W.sod(steps=1000)
+    s = F.Solver.from_workload(w, F.FDLBM_FP64)
+    s.step(w.steps)
+    rho, u, v, T = s.get_macro()
+    o = O.Sim(w.nx, 1, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc)
+    o.set_macro(*[a[:1] for a in w.macros()])
+    assert o.step(w.steps) == 0
+    ro, uo, vo, To = o.get_macro()
+    for got, ref in ((rho, ro), (u, uo), (v, vo), (T, To)):
+        assert _rel(got, np.broadcast_to(ref, got.shape)) <= 1e-11
+    for j in range(1, w.ny):
+        assert np.array_equal(rho[j], rho[0]) and np.array_equal(T[j], T[0])
+
+
+CASES = [
+    # nx, ny, bc, steps
+    (37, 23, (0, 0, 0, 0), 30),
+    (45, 19, (1, 2, 3, 1), 30),
+    (33, 9, (3, 3, 0, 0), 30),
+    (70, 37, (2, 1, 1, 3), 20),
+    (5, 3, (0, 0, 0, 0), 10),
+    (1, 6, (0, 0, 3, 2), 10),
+]
+
+
+@pytest.mark.parametrize("nx,ny,bc,steps", CASES)
+@pytest.mark.parametrize("variant", [0, 2, 3, 4])
+def test_fp64_f_matches_oracle_all_boundaries(nx, ny, bc, steps, variant):
+    """Every velocity at every node, every boundary kind, ragged tiles."""
+    bstate = np.zeros((4, 4))
+    for side in range(4):
+        bstate[side] = (1.1 + 0.1 * side, 0.2, -0.1, 0.9)
+    fields = _smooth(nx, ny, nx * 100 + ny)
+    s = F.Solver(nx, ny, 1e-3, 1.2e-3, 1e-5, 1.5e-5, 1.5, bc, F.FDLBM_FP64, 0, bstate)
+    s.set_variant(variant)
+    s.set_macro(*fields)
+    s.step(steps)
+    fg = s.get_f()
+    o = O.Sim(nx, ny, 1e-3, 1.2e-3, 1e-5, 1.5e-5, 1.5, bc, bstate)
+    o.set_macro(*fields)
+    assert o.step(steps) == 0
+    fo = o.get_f()
+    assert np.max(np.abs(fg - fo)) <= 1e-12 * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("flags", [O.NO_LW, O.NO_DISP, O.NO_VISC, O.SWITCH_CONST, O.NO_LW | O.NO_DISP | O.NO_VISC])
+def test_scheme_variants_match_oracle(flags):
+    """The Sec. 4 scheme variants (lines II/III/IV dropped, switch held at lambda)."""
+    nx, ny = 24, 16
+    fields = _smooth(nx, ny, 5, amp=0.2)
+    cfg = F.make_config(nx, ny, 1e-3, 1e-3, 1e-5, 1e-5, 0.8, (0, 0, 0, 0), F.FDLBM_FP64, flags)
+    h = F.fdlbm_create_ex(cfg)
+    try:
+        F.fdlbm_set_macro(h, *fields)
+        F.fdlbm_step(h, 15)
+        fg = F.fdlbm_get_f(h, nx, ny)
+    finally:
+        F.fdlbm_destroy(h)
+    o = O.Sim(nx, ny, 1e-3, 1e-3, 1e-5, 1e-5, 0.8, (0, 0, 0, 0), flags=flags)
+    o.set_macro(*fields)
+    assert o.step(15) == 0
+    fo = o.get_f()
+    assert np.max(np.abs(fg - fo)) <= 1e-12 * np.abs(fo).max()
+
+
+def test_variants_are_bitwise_identical():
+    """A node's arithmetic does not depend on the tile shape: all variants agree bit for bit."""
+    w = W.reflection(nx=300, ny=75, steps=40)
+    ref = None
+    for v in range(F.fdlbm_variant_count()):
+        s = F.Solver.from_workload(w, F.FDLBM_FP32_STORE)
+        s.set_variant(v)
+        s.step(w.steps)
+        f = s.get_f()
+        s.close()
+        if ref is None:
+            ref = f
+        else:
+            assert np.array_equal(f, ref), v
+
+
+def test_fp32_store_sod_error_is_stated():
+    """FP32 storage, FP64 moments and f_eq: L1(rho) relative error after 1000 Sod steps (kappa ~ 1)
+    stays below 1e-5, the target stated for Mach <= 5 states."""
+    w = W.sod(steps=1000)
+    s = F.Solver.from_workload(w, F.FDLBM_FP32_STORE)
+    s.step(w.steps)
+    rho, u, v, T = s.get_macro()
+    o = O.Sim(w.nx, 1, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc)
+    o.set_macro(*[a[:1] for a in w.macros()])
+    assert o.step(w.steps) == 0
+    ro, uo, vo, To = o.get_macro()
+    l1 = np.mean(np.abs(rho[0] - ro[0])) / np.mean(np.abs(ro[0]))
+    assert l1 <= 1e-5, l1
+    assert _rel(rho, np.broadcast_to(ro, rho.shape)) <= 1e-4
+
+
+def test_fp32_store_matches_oracle_on_small_grid():
+    """FP32 storage against FP64 on a smooth field: f agrees to ~1e-6 of max|f| after 20 steps."""
+    nx, ny = 40, 24
+    fields = _smooth(nx, ny, 21)
+    s = F.Solver(nx, ny, 1e-3, 1e-3, 1e-5, 1e-5, 1.0, (0, 0, 0, 0), F.FDLBM_FP32_STORE)
+    s.set_macro(*fields)
+    s.step(20)
+    fg = s.get_f()
+    o = O.Sim(nx, ny, 1e-3, 1e-3, 1e-5, 1e-5, 1.0, (0, 0, 0, 0))
+    o.set_macro(*fields)
+    assert o.step(20) == 0
+    fo = o.get_f()
+    assert np.max(np.abs(fg - fo)) <= 2e-6 * np.abs(fo).max()
+
+
+def test_numeric_failure_is_reported_like_the_oracle():
+    """Shock Mach 20 into gas at rest: the oracle rejects the second step (T <= 0); the GPU path
+    reports FDLBM_E_NUMERIC at the same point and refuses further steps (sticky)."""
+    w = W.shock_tube(nx=200, ny=4, steps=2, Ms=20.0, U=0.0, T1=1.0, lam=5.0)
+    s = F.Solver.from_workload(w, F.FDLBM_FP64)
+    s.step(1)
+    assert s.sync() == 0
+    s.step(1)
+    with pytest.raises(F.FdlbmError) as ei:
+        s.sync()
+    assert ei.value.code == F.FDLBM_E_NUMERIC
+    with pytest.raises(F.FdlbmError):
+        s.step(1)
+    assert s.health() & F.FDLBM_HEALTH_NUMERIC
+    # set_macro clears the sticky error
+    s.set_macro(*W.sod(nx=200, ny=4).macros())
+    s.step(3)
+    assert s.sync() == 0
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    w = W.reflection(nx=300, ny=75, steps=20)
+    for prec in (F.FDLBM_FP64, F.FDLBM_FP32_STORE):
+        a = F.Solver.from_workload(w, prec)
+        a.step(10)
+        path = str(tmp_path / ("ck%d.bin" % prec))
+        F.fdlbm_save(a.h, path)
+        a.step(10)
+        fa = a.get_f()
+        b = F.Solver(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, prec, 0, w.bstate)
+        F.fdlbm_load(b.h, path)
+        assert b.steps_done == 10
+        b.step(10)
+        assert np.array_equal(b.get_f(), fa)
+        # a checkpoint of another configuration is refused
+        c = F.Solver(w.nx + 1, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, prec, 0, w.bstate)
+        with pytest.raises(F.FdlbmError) as ei:
+            F.fdlbm_load(c.h, path)
+        assert ei.value.code == F.FDLBM_E_IO
+
+
+def test_device_pointer_calls_and_caller_stream():
+    """set/get_macro_device on torch tensors, ordered on a caller torch stream."""
+    w = W.sod(nx=128, ny=4, steps=50)
+    st = torch.cuda.Stream()
+    s = F.Solver(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, F.FDLBM_FP64, stream=st)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in w.macros()]
+    torch.cuda.synchronize()
+    F.fdlbm_set_macro_device(s.h, *dev)
+    s.step(w.steps)
+    outs = [torch.empty_like(d) for d in dev]
+    F.fdlbm_get_macro_device(s.h, *outs)
+    st.synchronize()
+    host = s.get_macro()
+    for d, hst in zip(outs, host):
+        assert np.array_equal(d.cpu().numpy(), hst)
+
+
+def test_autotune_keeps_state():
+    w = W.reflection(nx=300, ny=75, steps=10)
+    s = F.Solver.from_workload(w, F.FDLBM_FP32_STORE)
+    f0 = s.get_f()
+    times = s.autotune(3)
+    assert len(times) == F.fdlbm_variant_count() and all(t > 0 for t in times)
+    assert np.array_equal(s.get_f(), f0)
+    assert s.steps_done == 0
+
+
+def _window_step(f_full, node, w, flags=0):
+    """Oracle update of one node from the 5 x 5 window around it (its Eq. 17 dependence cone)."""
+    i, j = node
+    ny = f_full.shape[1]
+    rows = np.arange(j - 2, j + 3) % ny if w.bc[2] == O.PERIODIC else np.arange(j - 2, j + 3)
+    win = f_full[:, rows, :][:, :, i - 2:i + 3]
+    o = O.Sim(5, 5, w.dx, w.dy, w.dt, w.tau, w.lam, (0, 0, 0, 0), flags=flags)
+    o.set_f(win)
+    assert o.step(1) == 0
+    return o.get_f()[:, 2, 2]
+
+
+@pytest.mark.parametrize("name,prec", [("shock", F.FDLBM_FP64), ("shock", F.FDLBM_FP32_STORE),
+                                        ("reflection", F.FDLBM_FP32_STORE), ("reflection", F.FDLBM_FP64)])
+def test_full_size_sampled_one_step_parity(name, prec):
+    """At the full workload sizes in the default launch configuration: after a few hundred GPU
+    steps, one more GPU step agrees with the oracle's update of sampled nodes computed from the
+    GPU state (every node's update depends only on its 5 x 5 cross window)."""
+    w = W.shock_tube() if name == "shock" else W.reflection()
+    s = F.Solver.from_workload(w, prec)
+    s.step(300)
+    f0 = s.get_f()
+    s.step(1)
+    f1 = s.get_f()
+    assert s.sync() == 0
+    rng = np.random.default_rng(7)
+    periodic_y = w.bc[2] == O.PERIODIC
+    jlo, jhi = (0, w.ny) if periodic_y else (2, w.ny - 2)
+    nodes = [(int(rng.integers(2, w.nx - 2)), int(rng.integers(jlo, jhi))) for _ in range(60)]
+    tol = 1e-12 if prec == F.FDLBM_FP64 else 3e-6
+    for (i, j) in nodes:
+        ref = _window_step(f0, (i, j), w)
+        got = f1[:, j, i]
+        scale = np.abs(f0[:, :, i - 2:i + 3]).max()
+        assert np.max(np.abs(got - ref)) <= tol * scale, (i, j)
