@@ -154,6 +154,12 @@ int fdlbm_get_macro_device(fdlbm_t h, double* rho, double* u, double* v, double*
  * direction angle i*pi/4). Host arrays; synchronises. */
 int fdlbm_get_f(fdlbm_t h, double* f);
 
+/* Raw distribution of the node window [x0, x0+w) x [y0, y0+hgt), converted to FP64, layout
+ * [q][j][i] (33*w*hgt doubles). The window may reach into the ghost ring
+ * (-2 <= x0, x0+w <= nx+2, same for y); ghost corners hold unspecified values. Host array;
+ * synchronises. FDLBM_E_ARG if the window leaves that range or is empty. */
+int fdlbm_get_f_region(fdlbm_t h, int x0, int y0, int w, int hgt, double* f);
+
 /* Set the raw interior distribution (same layout; rounded to the storage
  * precision) and refill the ghost ring. Host array; synchronises. */
 int fdlbm_set_f(fdlbm_t h, const double* f);

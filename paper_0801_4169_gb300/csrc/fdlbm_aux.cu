@@ -1,0 +1,81 @@
+// fdlbm_aux.cu -- launchers of the step dispatch and of the auxiliary kernels (initial condition,
+// Dirichlet ghosts, moments out, raw f copies); templates in fdlbm_kernels.cuh.
+#include "fdlbm_kernels.cuh"
+
+namespace fdlbm {
+
+cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
+                        unsigned* health, cudaStream_t s) {
+  return prec == 0 ? launch_step_f64(variant, f, fn, g, c, health, s)
+                   : launch_step_f32(variant, f, fn, g, c, health, s);
+}
+
+cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
+                        const double* v, const double* T, cudaStream_t s) {
+  dim3 b(32, 4);
+  if (prec == 0)
+    k_init<double><<<grid2d(g, b), b, 0, s>>>(static_cast<double*>(f), g, c, rho, u, v, T);
+  else
+    k_init<float><<<grid2d(g, b), b, 0, s>>>(static_cast<float*>(f), g, c, rho, u, v, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dirichlet(int prec, void* f, const Grid& g, const Coeffs& c, const double bstate[4][4],
+                             cudaStream_t s) {
+  BState bs;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) bs.s[i][j] = bstate[i][j];
+  const int len = 2 * (g.nx > g.ny ? g.nx : g.ny);
+  dim3 b(128), grid((len + 127) / 128, 4);
+  if (prec == 0)
+    k_dirichlet<double><<<grid, b, 0, s>>>(static_cast<double*>(f), g, c, bs);
+  else
+    k_dirichlet<float><<<grid, b, 0, s>>>(static_cast<float*>(f), g, c, bs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_macro(int prec, const void* f, const Grid& g, double* rho, double* u, double* v, double* T,
+                         cudaStream_t s) {
+  dim3 b(32, 4);
+  Coeffs c{};
+  const double sp[4] = {1.0, 1.92, 2.99, 4.49};
+  for (int k = 0; k < 4; ++k) {
+    c.v[k] = sp[k];
+    c.v2[k] = sp[k] * sp[k];
+  }
+  if (prec == 0)
+    k_macro<double><<<grid2d(g, b), b, 0, s>>>(static_cast<const double*>(f), g, c, rho, u, v, T);
+  else
+    k_macro<float><<<grid2d(g, b), b, 0, s>>>(static_cast<const float*>(f), g, c, rho, u, v, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_f(int prec, const void* f, const Grid& g, double* out, cudaStream_t s) {
+  dim3 b(32, 4);
+  if (prec == 0)
+    k_get_f<double><<<grid2d(g, b), b, 0, s>>>(static_cast<const double*>(f), g, out);
+  else
+    k_get_f<float><<<grid2d(g, b), b, 0, s>>>(static_cast<const float*>(f), g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_region(int prec, const void* f, const Grid& g, int x0, int y0, int w, int h, double* out,
+                              cudaStream_t s) {
+  dim3 b(32, 4), grid((w + 31) / 32, (h + 3) / 4);
+  if (prec == 0)
+    k_get_region<double><<<grid, b, 0, s>>>(static_cast<const double*>(f), g, x0, y0, w, h, out);
+  else
+    k_get_region<float><<<grid, b, 0, s>>>(static_cast<const float*>(f), g, x0, y0, w, h, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_f(int prec, void* f, const Grid& g, const double* in, cudaStream_t s) {
+  dim3 b(32, 4);
+  if (prec == 0)
+    k_set_f<double><<<grid2d(g, b), b, 0, s>>>(static_cast<double*>(f), g, in);
+  else
+    k_set_f<float><<<grid2d(g, b), b, 0, s>>>(static_cast<float*>(f), g, in);
+  return cudaGetLastError();
+}
+
+}  // namespace fdlbm

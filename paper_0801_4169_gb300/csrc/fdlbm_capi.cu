@@ -27,7 +27,8 @@ struct fdlbm_ctx {
   int cur = 0;
   unsigned* d_health = nullptr;
   double* d_stage = nullptr;   // 4 * nx * ny doubles for host-pointer macro calls
-  double* d_fstage = nullptr;  // 33 * nx * ny doubles for get_f / set_f (allocated on first use)
+  double* d_fstage = nullptr;  // staging for get_f / set_f / get_f_region (allocated on first use)
+  size_t fstage_cap = 0;       // doubles
   unsigned* h_health = nullptr;  // pinned
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
@@ -147,6 +148,9 @@ Coeffs make_coeffs(const fdlbm_config* cfg) {
   c.kx = kk[0];
   c.ky = kk[1];
   c.lam = cfg->lambda;
+  c.fkx = (float)c.kx;
+  c.fky = (float)c.ky;
+  c.flam = (float)c.lam;
   return c;
 }
 
@@ -211,16 +215,24 @@ int init_from_device_macros(fdlbm_ctx* h, const double* rho, const double* u, co
   return FDLBM_OK;
 }
 
-int ensure_fstage(fdlbm_ctx* h) {
-  if (h->d_fstage) return FDLBM_OK;
-  cudaError_t e = cudaMalloc(&h->d_fstage, (size_t)Q * h->cfg.nx * h->cfg.ny * sizeof(double));
+int ensure_fstage(fdlbm_ctx* h, size_t ndoubles) {
+  if (h->d_fstage && h->fstage_cap >= ndoubles) return FDLBM_OK;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "staging sync");
+  if (h->d_fstage) cudaFree(h->d_fstage);
+  h->d_fstage = nullptr;
+  h->fstage_cap = 0;
+  e = cudaMalloc(&h->d_fstage, ndoubles * sizeof(double));
   if (e != cudaSuccess) {
     h->d_fstage = nullptr;
     cudaGetLastError();
     return fail(h, FDLBM_E_OOM, "cannot allocate the f staging buffer");
   }
+  h->fstage_cap = ndoubles;
   return FDLBM_OK;
 }
+
+size_t full_f_doubles(const fdlbm_ctx* h) { return (size_t)Q * h->cfg.nx * h->cfg.ny; }
 
 struct CkptHeader {
   char magic[8];
@@ -409,7 +421,7 @@ int fdlbm_get_f(fdlbm_t h, double* f) {
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!f) return fail(h, FDLBM_E_ARG, "f is NULL");
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "no state yet");
-  int rc = ensure_fstage(h);
+  int rc = ensure_fstage(h, full_f_doubles(h));
   if (rc) return rc;
   cudaError_t e = launch_get_f(h->cfg.prec, h->f[h->cur], h->grid, h->d_fstage, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_f launch");
@@ -419,10 +431,27 @@ int fdlbm_get_f(fdlbm_t h, double* f) {
   return fdlbm_sync(h);
 }
 
+int fdlbm_get_f_region(fdlbm_t h, int x0, int y0, int w, int hgt, double* f) {
+  if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
+  if (!f) return fail(h, FDLBM_E_ARG, "f is NULL");
+  if (!h->initialised) return fail(h, FDLBM_E_STATE, "no state yet");
+  if (w < 1 || hgt < 1 || x0 < -NG || y0 < -NG || (long long)x0 + w > (long long)h->cfg.nx + NG ||
+      (long long)y0 + hgt > (long long)h->cfg.ny + NG)
+    return fail(h, FDLBM_E_ARG, "region outside the padded grid [-2, n+2)");
+  const size_t nd = (size_t)Q * w * hgt;
+  int rc = ensure_fstage(h, nd);
+  if (rc) return rc;
+  cudaError_t e = launch_get_region(h->cfg.prec, h->f[h->cur], h->grid, x0, y0, w, hgt, h->d_fstage, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_f_region launch");
+  e = cudaMemcpyAsync(f, h->d_fstage, nd * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_f_region copy");
+  return fdlbm_sync(h);
+}
+
 int fdlbm_set_f(fdlbm_t h, const double* f) {
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!f) return fail(h, FDLBM_E_ARG, "f is NULL");
-  int rc = ensure_fstage(h);
+  int rc = ensure_fstage(h, full_f_doubles(h));
   if (rc) return rc;
   poll_health(h, true);
   cudaError_t e = cudaMemcpyAsync(h->d_fstage, f, (size_t)Q * h->cfg.nx * h->cfg.ny * sizeof(double),

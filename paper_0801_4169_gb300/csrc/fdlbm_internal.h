@@ -51,13 +51,23 @@ struct Coeffs {
   double lam;           // lambda of Eq. 16
   // FP32 copies used by the FP32-storage stencil
   float fW1[2][4][2], fWm1[2][4][2], fD[2][4][2], fC2[4][3];
-  float fr;
+  float fr, fkx, fky, flam;
 };
 
-// Launch configuration of the fused step (tile of TW x TH nodes per CTA).
-enum StepVariant { V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_COUNT = 5 };
+// Launch configuration of the fused step: tile of TW x TH nodes per CTA. Variants 0-5 cap the
+// registers at 128 per thread (2-4 CTAs per SM); the _R variants leave the allocation free
+// (one 256-thread CTA per SM, no spills).
+enum StepVariant {
+  V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_T32x32 = 5, V_T32x16_R = 6,
+  V_T32x32_R = 7, V_COUNT = 8
+};
 
-// Kernel launchers (fdlbm_step.cu). All return cudaGetLastError() of the launch.
+// Kernel launchers (fdlbm_aux.cu, fdlbm_step_f32.cu, fdlbm_step_f64.cu). All return
+// cudaGetLastError() of the launch.
+cudaError_t launch_step_f64(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
+                            cudaStream_t s);
+cudaError_t launch_step_f32(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
+                            cudaStream_t s);
 cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
                         unsigned* health, cudaStream_t s);
 cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
@@ -67,6 +77,8 @@ cudaError_t launch_dirichlet(int prec, void* f, const Grid& g, const Coeffs& c, 
 cudaError_t launch_macro(int prec, const void* f, const Grid& g, double* rho, double* u, double* v, double* T,
                          cudaStream_t s);
 cudaError_t launch_get_f(int prec, const void* f, const Grid& g, double* out, cudaStream_t s);
+cudaError_t launch_get_region(int prec, const void* f, const Grid& g, int x0, int y0, int w, int h, double* out,
+                              cudaStream_t s);
 cudaError_t launch_set_f(int prec, void* f, const Grid& g, const double* in, cudaStream_t s);
 
 }  // namespace fdlbm

@@ -1,4 +1,7 @@
-// fdlbm_step.cu -- sm_103a kernels of the FDLBM step (Gan, Xu, Zhang, Yu, Li, arXiv 0801.4169).
+#pragma once
+// fdlbm_kernels.cuh -- sm_103a kernels of the FDLBM step (Gan, Xu, Zhang, Yu, Li, arXiv 0801.4169).
+// Included by fdlbm_step_f64.cu / fdlbm_step_f32.cu (one precision each, compiled in parallel)
+// and fdlbm_aux.cu (initial condition, boundary, moment and copy kernels).
 //
 // One fused kernel per time step computes, for every interior node of its tile:
 //   moments n, u, T, P of Eqs. 3-5            (FP64, tile + 1-node ring, staged in shared memory)
@@ -31,12 +34,37 @@ __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }
 
+// FP32 <-> FP64 conversions issue on the (slow) FP64 pipe. For normal numbers both directions
+// are done bit-exactly with integer operations instead; zero, subnormal, inf/nan and values
+// outside the FP32 normal range take the hardware conversion.
+//   up:   exponent += 1023 - 127, mantissa shifted left by 29 (exact).
+//   down: round to nearest even on the 29 dropped mantissa bits (a carry into the exponent is
+//         the correct rounding, up to +inf).
+__device__ __forceinline__ bool f32_special(float x) {
+  const unsigned a = __float_as_uint(x) & 0x7fffffffu;
+  return a - 0x00800000u >= 0x7f000000u;  // a < 2^-126 (zero/subnormal) or inf/nan
+}
+__device__ __forceinline__ double f32_to_f64_bits(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ah = hi & 0x7fffffffu;
+  if (ah - (897u << 20) >= (254u << 20)) return __double2float_rn(x);  // not an FP32 normal
+  unsigned t = ((ah - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  t += (rem > 0x10000000u) | ((rem == 0x10000000u) & (t & 1u));
+  return __uint_as_float(t | (hi & 0x80000000u));
+}
+
 template <typename S>
 __device__ __forceinline__ S from_d(double x);
 template <>
 __device__ __forceinline__ double from_d<double>(double x) { return x; }
 template <>
-__device__ __forceinline__ float from_d<float>(double x) { return __double2float_rn(x); }
+__device__ __forceinline__ float from_d<float>(double x) { return f64_to_f32_rn(x); }
 
 // ---------------------------------------------------------------------------------------------
 // Velocity ordering (Eq. 1): q = 0 rest, q = 1 + 8k + d for ring k = 0..3 (speed v_{k+1}) and
@@ -142,10 +170,10 @@ __device__ __forceinline__ void ring_moments(const double g[8], double vk, doubl
   m.e2 = fma(vk2, S, m.e2);
 }
 
-template <typename S>
-__device__ __forceinline__ Mom node_moments(const S* __restrict__ f, long long plane, long long off, const Coeffs& c) {
+__device__ __forceinline__ Mom node_moments(const double* __restrict__ f, long long plane, long long off,
+                                            const Coeffs& c) {
   Mom m;
-  m.n = to_d(ld(f + off));
+  m.n = ld(f + off);
   m.jx = 0.0;
   m.jy = 0.0;
   m.e2 = 0.0;
@@ -153,8 +181,44 @@ __device__ __forceinline__ Mom node_moments(const S* __restrict__ f, long long p
   for (int k = 0; k < 4; ++k) {
     double g[8];
 #pragma unroll
-    for (int d = 0; d < 8; ++d) g[d] = to_d(ld(f + (long long)(1 + 8 * k + d) * plane + off));
+    for (int d = 0; d < 8; ++d) g[d] = ld(f + (long long)(1 + 8 * k + d) * plane + off);
     ring_moments(g, c.v[k], c.v2[k], m);
+  }
+  return m;
+}
+
+// FP32 storage: the 33 values are widened to FP64 exactly (integer path), then summed in FP64.
+__device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long long plane, long long off,
+                                            const Coeffs& c) {
+  float x[Q];
+  bool special = false;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    x[q] = ld(f + (long long)q * plane + off);
+    special |= f32_special(x[q]);
+  }
+  Mom m;
+  m.jx = 0.0;
+  m.jy = 0.0;
+  m.e2 = 0.0;
+  if (!special) {
+    m.n = f32_to_f64_bits(x[0]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double g[8];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) g[d] = f32_to_f64_bits(x[1 + 8 * k + d]);
+      ring_moments(g, c.v[k], c.v2[k], m);
+    }
+  } else {
+    m.n = (double)x[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double g[8];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) g[d] = (double)x[1 + 8 * k + d];
+      ring_moments(g, c.v[k], c.v2[k], m);
+    }
   }
   return m;
 }
@@ -290,6 +354,9 @@ struct StencilConsts<double> {
   __device__ static double D(const Coeffs& c, int a, int k, int l) { return c.D[a][k][l]; }
   __device__ static double C2(const Coeffs& c, int k, int l) { return c.C2[k][l]; }
   __device__ static double r(const Coeffs& c) { return c.r; }
+  __device__ static double kx(const Coeffs& c) { return c.kx; }
+  __device__ static double ky(const Coeffs& c) { return c.ky; }
+  __device__ static double lam(const Coeffs& c) { return c.lam; }
 };
 template <>
 struct StencilConsts<float> {
@@ -298,6 +365,9 @@ struct StencilConsts<float> {
   __device__ static float D(const Coeffs& c, int a, int k, int l) { return c.fD[a][k][l]; }
   __device__ static float C2(const Coeffs& c, int k, int l) { return c.fC2[k][l]; }
   __device__ static float r(const Coeffs& c) { return c.fr; }
+  __device__ static float kx(const Coeffs& c) { return c.fkx; }
+  __device__ static float ky(const Coeffs& c) { return c.fky; }
+  __device__ static float lam(const Coeffs& c) { return c.flam; }
 };
 
 // Update of all 33 velocities at one interior node, given its moments and nu_x, nu_y.
@@ -356,11 +426,15 @@ __device__ __forceinline__ S to_s(double x) { return from_d<S>(x); }
 // ---------------------------------------------------------------------------------------------
 // The fused step. CTA = BX x BY threads; tile TW x TH = BX x (BY*RY) nodes. Shared memory holds
 // n, ux, uy, T, P of the tile and its 1-node ring (corners excluded), computed once per node.
-template <typename S, int BX, int BY, int RY>
-__global__ void __launch_bounds__(BX * BY) k_step(const S* __restrict__ f, S* __restrict__ fn, Grid g, Coeffs c,
+template <typename S, int BX, int BY, int RY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f, S* __restrict__ fn, Grid g, Coeffs c,
                                                   unsigned* __restrict__ health) {
   constexpr int TW = BX, TH = BY * RY, SW = TW + 2, SH = TH + 2, NT = BX * BY;
-  __shared__ double s_n[SH][SW], s_ux[SH][SW], s_uy[SH][SW], s_T[SH][SW], s_P[SH][SW];
+  using SC = StencilConsts<S>;
+  // P is staged in the storage precision: the switch of Eq. 16 is a limiter coefficient, and in
+  // the FP32-storage path it is evaluated in FP32 like the rest of the stencil weights.
+  __shared__ double s_n[SH][SW], s_ux[SH][SW], s_uy[SH][SW], s_T[SH][SW];
+  __shared__ S s_P[SH][SW];
   const int tid = threadIdx.y * BX + threadIdx.x;
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
   unsigned bits = 0;
@@ -374,13 +448,13 @@ __global__ void __launch_bounds__(BX * BY) k_step(const S* __restrict__ f, S* __
     const bool need = (inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny));
     if (!need) continue;
     const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
-    const Macro m = to_macro(node_moments<S>(f, g.plane, off, c));
+    const Macro m = to_macro(node_moments(f, g.plane, off, c));
     if (!macro_ok(m)) bits |= H_NUMERIC;
     s_n[ly][lx] = m.n;
     s_ux[ly][lx] = m.ux;
     s_uy[ly][lx] = m.uy;
     s_T[ly][lx] = m.T;
-    s_P[ly][lx] = m.P;
+    s_P[ly][lx] = from_d<S>(m.P);
   }
   __syncthreads();
 
@@ -390,28 +464,26 @@ __global__ void __launch_bounds__(BX * BY) k_step(const S* __restrict__ f, S* __
     const int lx = threadIdx.x + 1, ly = threadIdx.y + rr * BY + 1;
     const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + rr * BY;
     if (gx >= g.nx || gy >= g.ny) continue;
-    const double n = s_n[ly][lx], ux = s_ux[ly][lx], uy = s_uy[ly][lx], T = s_T[ly][lx], P0 = s_P[ly][lx];
-    // switch of Eq. 16 and kappa of Eq. 15
-    double thx, thy;
+    const double n = s_n[ly][lx], ux = s_ux[ly][lx], uy = s_uy[ly][lx], T = s_T[ly][lx];
+    // switch of Eq. 16 and kappa of Eq. 15 (storage precision)
+    S thx, thy;
     if (g.flags & F_SWITCH_CONST) {
-      thx = c.lam;
-      thy = c.lam;
+      thx = SC::lam(c);
+      thy = SC::lam(c);
     } else {
-      const double Pxp = s_P[ly][lx + 1], Pxm = s_P[ly][lx - 1];
-      const double Pyp = s_P[ly + 1][lx], Pym = s_P[ly - 1][lx];
-      const double sx = Pxp + Pxm, sy = Pyp + Pym;
-      thx = c.lam * fabs(fma(-2.0, P0, sx) / fma(2.0, P0, sx));
-      thy = c.lam * fabs(fma(-2.0, P0, sy) / fma(2.0, P0, sy));
+      const S P0 = s_P[ly][lx];
+      const S sx = s_P[ly][lx + 1] + s_P[ly][lx - 1], sy = s_P[ly + 1][lx] + s_P[ly - 1][lx];
+      thx = SC::lam(c) * fabs(fma((S)-2, P0, sx) / fma((S)2, P0, sx));
+      thy = SC::lam(c) * fabs(fma((S)-2, P0, sy) / fma((S)2, P0, sy));
     }
-    const double akx = fabs(ux * c.kx), aky = fabs(uy * c.ky);
-    if (akx > 1.0 || aky > 1.0) bits |= H_KAPPA;
-    double nux = 0.0, nuy = 0.0;
+    const S akx = fabs(from_d<S>(ux) * SC::kx(c)), aky = fabs(from_d<S>(uy) * SC::ky(c));
+    if (akx > (S)1 || aky > (S)1) bits |= H_KAPPA;
+    S snux = 0, snuy = 0;
     if (!(g.flags & F_NO_VISC)) {
-      nux = 0.5 * thx * akx * (1.0 - akx);
-      nuy = 0.5 * thy * aky * (1.0 - aky);
+      snux = (S)0.5 * thx * akx * ((S)1 - akx);
+      snuy = (S)0.5 * thy * aky * ((S)1 - aky);
     }
-    const S snux = to_s<S>(nux), snuy = to_s<S>(nuy);
-    const S w0base = to_s<S>(1.0 - c.r) - (S)2 * (snux + snuy);
+    const S w0base = ((S)1 - SC::r(c)) - (S)2 * (snux + snuy);
     const EqSite e = eq_site(n, ux, uy, T, c);
     const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
     const GhostOwn go = ghost_own(g, gx, gy);
@@ -506,7 +578,7 @@ __global__ void k_macro(const S* __restrict__ f, Grid g, Coeffs c, double* __res
   const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
   if (gx >= g.nx || gy >= g.ny) return;
   const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
-  const Macro m = to_macro(node_moments<S>(f, g.plane, off, c));
+  const Macro m = to_macro(node_moments(f, g.plane, off, c));
   const long long o = (long long)gy * g.nx + gx;
   rho[o] = m.n;
   u[o] = m.ux;
@@ -520,6 +592,14 @@ __global__ void k_get_f(const S* __restrict__ f, Grid g, double* __restrict__ ou
   if (gx >= g.nx || gy >= g.ny) return;
   const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
   for (int q = 0; q < Q; ++q) out[((long long)q * g.ny + gy) * g.nx + gx] = to_d(f[(long long)q * g.plane + off]);
+}
+
+template <typename S>
+__global__ void k_get_region(const S* __restrict__ f, Grid g, int x0, int y0, int w, int h, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= w || j >= h) return;
+  const long long off = (long long)(y0 + j + NG) * g.pitch + (x0 + i + NG);
+  for (int q = 0; q < Q; ++q) out[((long long)q * h + j) * w + i] = to_d(f[(long long)q * g.plane + off]);
 }
 
 template <typename S, int QQ>
@@ -539,12 +619,13 @@ __global__ void k_set_f(S* __restrict__ f, Grid g, const double* __restrict__ in
           29, 30, 31, 32>(f, g, gx, gy, go, in);
 }
 
-template <typename S, int BX, int BY, int RY>
+// MINB: CTAs per SM the register allocation must allow (1 = no cap, 2 or 4 = <= 128 registers).
+template <typename S, int BX, int BY, int RY, int MINB>
 cudaError_t launch_step_t(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
   dim3 block(BX, BY);
   dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY * RY - 1) / (BY * RY));
-  k_step<S, BX, BY, RY><<<grid, block, 0, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g, c, health);
+  k_step<S, BX, BY, RY, MINB><<<grid, block, 0, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g, c, health);
   return cudaGetLastError();
 }
 
@@ -552,81 +633,19 @@ template <typename S>
 cudaError_t launch_step_v(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
   switch (variant) {
-    case V_T32x4: return launch_step_t<S, 32, 4, 1>(f, fn, g, c, health, s);
-    case V_T32x8: return launch_step_t<S, 32, 4, 2>(f, fn, g, c, health, s);
-    case V_T32x16: return launch_step_t<S, 32, 8, 2>(f, fn, g, c, health, s);
-    case V_T16x4: return launch_step_t<S, 16, 4, 1>(f, fn, g, c, health, s);
-    case V_T64x8: return launch_step_t<S, 64, 4, 2>(f, fn, g, c, health, s);
+    case V_T32x4: return launch_step_t<S, 32, 4, 1, 4>(f, fn, g, c, health, s);
+    case V_T32x8: return launch_step_t<S, 32, 4, 2, 4>(f, fn, g, c, health, s);
+    case V_T32x16: return launch_step_t<S, 32, 8, 2, 2>(f, fn, g, c, health, s);
+    case V_T16x4: return launch_step_t<S, 16, 4, 1, 1>(f, fn, g, c, health, s);
+    case V_T64x8: return launch_step_t<S, 64, 4, 2, 2>(f, fn, g, c, health, s);
+    case V_T32x32: return launch_step_t<S, 32, 8, 4, 2>(f, fn, g, c, health, s);
+    case V_T32x16_R: return launch_step_t<S, 32, 8, 2, 1>(f, fn, g, c, health, s);
+    case V_T32x32_R: return launch_step_t<S, 32, 8, 4, 1>(f, fn, g, c, health, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-dim3 grid2d(const Grid& g, dim3 b) { return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y); }
+inline dim3 grid2d(const Grid& g, dim3 b) { return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y); }
 
 }  // namespace
-
-cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
-                        unsigned* health, cudaStream_t s) {
-  return prec == 0 ? launch_step_v<double>(variant, f, fn, g, c, health, s)
-                   : launch_step_v<float>(variant, f, fn, g, c, health, s);
-}
-
-cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
-                        const double* v, const double* T, cudaStream_t s) {
-  dim3 b(32, 4);
-  if (prec == 0)
-    k_init<double><<<grid2d(g, b), b, 0, s>>>(static_cast<double*>(f), g, c, rho, u, v, T);
-  else
-    k_init<float><<<grid2d(g, b), b, 0, s>>>(static_cast<float*>(f), g, c, rho, u, v, T);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_dirichlet(int prec, void* f, const Grid& g, const Coeffs& c, const double bstate[4][4],
-                             cudaStream_t s) {
-  BState bs;
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) bs.s[i][j] = bstate[i][j];
-  const int len = 2 * (g.nx > g.ny ? g.nx : g.ny);
-  dim3 b(128), grid((len + 127) / 128, 4);
-  if (prec == 0)
-    k_dirichlet<double><<<grid, b, 0, s>>>(static_cast<double*>(f), g, c, bs);
-  else
-    k_dirichlet<float><<<grid, b, 0, s>>>(static_cast<float*>(f), g, c, bs);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_macro(int prec, const void* f, const Grid& g, double* rho, double* u, double* v, double* T,
-                         cudaStream_t s) {
-  dim3 b(32, 4);
-  Coeffs c{};
-  const double sp[4] = {1.0, 1.92, 2.99, 4.49};
-  for (int k = 0; k < 4; ++k) {
-    c.v[k] = sp[k];
-    c.v2[k] = sp[k] * sp[k];
-  }
-  if (prec == 0)
-    k_macro<double><<<grid2d(g, b), b, 0, s>>>(static_cast<const double*>(f), g, c, rho, u, v, T);
-  else
-    k_macro<float><<<grid2d(g, b), b, 0, s>>>(static_cast<const float*>(f), g, c, rho, u, v, T);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_get_f(int prec, const void* f, const Grid& g, double* out, cudaStream_t s) {
-  dim3 b(32, 4);
-  if (prec == 0)
-    k_get_f<double><<<grid2d(g, b), b, 0, s>>>(static_cast<const double*>(f), g, out);
-  else
-    k_get_f<float><<<grid2d(g, b), b, 0, s>>>(static_cast<const float*>(f), g, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_set_f(int prec, void* f, const Grid& g, const double* in, cudaStream_t s) {
-  dim3 b(32, 4);
-  if (prec == 0)
-    k_set_f<double><<<grid2d(g, b), b, 0, s>>>(static_cast<double*>(f), g, in);
-  else
-    k_set_f<float><<<grid2d(g, b), b, 0, s>>>(static_cast<float*>(f), g, in);
-  return cudaGetLastError();
-}
-
 }  // namespace fdlbm

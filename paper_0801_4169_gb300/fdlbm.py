@@ -70,6 +70,7 @@ def lib():
             "fdlbm_get_macro_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
             "fdlbm_get_f": (ctypes.c_int, [_VP, _DP]),
             "fdlbm_set_f": (ctypes.c_int, [_VP, _DP]),
+            "fdlbm_get_f_region": (ctypes.c_int, [_VP] + [ctypes.c_int] * 4 + [_DP]),
             "fdlbm_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
             "fdlbm_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
             "fdlbm_variant_count": (ctypes.c_int, []),
@@ -194,6 +195,12 @@ def fdlbm_get_f(h, nx, ny):
     return f
 
 
+def fdlbm_get_f_region(h, x0, y0, w, hgt):
+    f = np.empty((Q, hgt, w))
+    _check(h, lib().fdlbm_get_f_region(h, int(x0), int(y0), int(w), int(hgt), _hp(f)))
+    return f
+
+
 def fdlbm_set_f(h, f):
     f = np.ascontiguousarray(f, dtype=np.float64)
     return _check(h, lib().fdlbm_set_f(h, _hp(f)))
@@ -296,6 +303,9 @@ class Solver:
 
     def set_f(self, f):
         return fdlbm_set_f(self.h, f)
+
+    def get_f_region(self, x0, y0, w, hgt):
+        return fdlbm_get_f_region(self.h, x0, y0, w, hgt)
 
     def set_variant(self, v):
         return fdlbm_set_variant(self.h, v)
