@@ -188,6 +188,42 @@ long fdlbm_steps_done(fdlbm_t h);
 /* Health bits (enum fdlbm_health_bits) accumulated since set_macro; synchronises. */
 unsigned fdlbm_health(fdlbm_t h);
 
+/* Largest nsteps one fdlbm_step_noalloc call accepts (its static scratch holds one word per step). */
+#define FDLBM_NOALLOC_MAX_STEPS 4096
+
+/* The fused step for callers that cannot allocate device memory. The paper has no counterpart;
+ * this is a service of the library.
+ *
+ * Who needs it: a caller whose device memory all belongs to another allocator (a framework's
+ * caching pool, a fixed arena set up at start-up), or whose path must not call cudaMalloc
+ * (which can synchronise the device or fail under a memory cap). Such a caller owns both state
+ * buffers and passes them in. The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine. The step's only scratch, one health word per step, is a
+ * file-scope __device__ array of FDLBM_NOALLOC_MAX_STEPS words (16 KiB), which every GPU that
+ * loads the library holds until the process exits.
+ *
+ * cfg      the problem (as for fdlbm_create_ex).
+ * f_a      the current state, in the layout the handle calls use: 33 planes f[q][j+2][i+2] of
+ *          (ny+4) rows x pitch elements, pitch = (nx+4) rounded up to a multiple of 32, in the
+ *          storage precision of cfg->prec. Device memory, 256-byte aligned. Its ghost ring must
+ *          be filled (e.g. it was produced by a handle, or copied from one).
+ * f_b      the second buffer of the pair, same size and alignment, with the same Dirichlet
+ *          ghosts as f_a (steps rewrite every other ghost).
+ * nsteps   0..FDLBM_NOALLOC_MAX_STEPS; larger values return FDLBM_E_ARG. Steps alternate
+ *          f_a -> f_b -> f_a ...; the result is in f_a if nsteps is even, in f_b if odd.
+ * first_bad_step  may be NULL; receives the index of the first step whose input held a node with
+ *          non-finite moments, n <= 0 or T <= 0 (then FDLBM_E_NUMERIC is returned), else -1.
+ * cuda_stream  a cudaStream_t or NULL; the call synchronises it before returning.
+ *
+ * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture. Every call on a
+ * device shares the one array and clears the words it uses at its start: calls that overlap on
+ * the GPU (different streams or threads) race on it. Errors: FDLBM_E_ARG (invalid cfg, NULL or
+ * misaligned buffers, nsteps out of range), FDLBM_E_NUMERIC, FDLBM_E_CUDA; the message is in
+ * fdlbm_last_error(NULL). */
+int fdlbm_step_noalloc(const fdlbm_config* cfg, void* f_a, void* f_b, long nsteps, long* first_bad_step,
+                       void* cuda_stream);
+
 /* Release the handle and the memory it owns. NULL-safe. */
 int fdlbm_destroy(fdlbm_t h);
 

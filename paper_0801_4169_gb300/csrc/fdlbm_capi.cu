@@ -46,6 +46,14 @@ namespace {
 
 thread_local std::string g_create_err;
 
+}  // namespace
+
+namespace fdlbm {
+void set_thread_error(const char* msg) { g_create_err = msg; }
+}  // namespace fdlbm
+
+namespace {
+
 int fail(fdlbm_ctx* h, int code, const std::string& msg) {
   if (h) h->err = msg;
   else g_create_err = msg;
@@ -59,6 +67,10 @@ int cuda_fail(fdlbm_ctx* h, cudaError_t e, const char* what) {
 }
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+namespace fdlbm {
 
 bool valid_cfg(const fdlbm_config* c, std::string* why) {
   if (!c) { *why = "config is NULL"; return false; }
@@ -76,11 +88,6 @@ bool valid_cfg(const fdlbm_config* c, std::string* why) {
   if ((c->bc[2] == FDLBM_BC_WALL || c->bc[3] == FDLBM_BC_WALL) && c->ny < 2) { *why = "a wall in y needs ny >= 2"; return false; }
   return true;
 }
-
-struct Layout {
-  Grid g;
-  size_t esize, fbytes, health_off, stage_off, total;
-};
 
 Layout layout_of(const fdlbm_config* c) {
   Layout L;
@@ -160,6 +167,10 @@ int default_variant(const fdlbm_config* c) {
   if (sites < 200000) return V_T32x8;
   return V_T32x16;
 }
+
+}  // namespace fdlbm
+
+namespace {
 
 // Collect a finished health copy, if any, into the sticky status.
 void poll_health(fdlbm_ctx* h, bool wait) {

@@ -3,7 +3,12 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
+
+#include <string>
+
+#include "../../include/fdlbm.h"
 
 namespace fdlbm {
 
@@ -80,5 +85,16 @@ cudaError_t launch_get_f(int prec, const void* f, const Grid& g, double* out, cu
 cudaError_t launch_get_region(int prec, const void* f, const Grid& g, int x0, int y0, int w, int h, double* out,
                               cudaStream_t s);
 cudaError_t launch_set_f(int prec, void* f, const Grid& g, const double* in, cudaStream_t s);
+
+// Host helpers shared by the C ABI files (fdlbm_capi.cu).
+struct Layout {
+  Grid g;
+  size_t esize, fbytes, health_off, stage_off, total;
+};
+bool valid_cfg(const fdlbm_config* c, std::string* why);
+Layout layout_of(const fdlbm_config* c);
+Coeffs make_coeffs(const fdlbm_config* cfg);
+int default_variant(const fdlbm_config* c);
+void set_thread_error(const char* msg);  // message returned by fdlbm_last_error(NULL)
 
 }  // namespace fdlbm

@@ -82,6 +82,7 @@ def lib():
             "fdlbm_destroy": (ctypes.c_int, [_VP]),
             "fdlbm_last_error": (ctypes.c_char_p, [_VP]),
             "fdlbm_version": (ctypes.c_char_p, []),
+            "fdlbm_step_noalloc": (ctypes.c_int, [cfgp, _VP, _VP, ctypes.c_long, ctypes.POINTER(ctypes.c_long), _VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -251,6 +252,23 @@ def fdlbm_last_error(h):
     return s.decode() if s else ""
 
 
+FDLBM_NOALLOC_MAX_STEPS = 4096
+
+
+def fdlbm_step_noalloc(cfg, f_a, f_b, nsteps, stream=None):
+    """Allocation-free fused step on caller buffers; returns first_bad_step (-1 if none).
+
+    Raises FdlbmError (FDLBM_E_NUMERIC carries the step in .first_bad_step)."""
+    bad = ctypes.c_long(-1)
+    rc = lib().fdlbm_step_noalloc(ctypes.byref(cfg), _dptr(f_a), _dptr(f_b), int(nsteps), ctypes.byref(bad),
+                                  _stream_ptr(stream))
+    if rc < 0:
+        err = FdlbmError(rc, fdlbm_last_error(None))
+        err.first_bad_step = bad.value
+        raise err
+    return bad.value
+
+
 def fdlbm_version():
     return lib().fdlbm_version().decode()
 
@@ -271,6 +289,7 @@ class Solver:
             self._mem = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
             base = self._mem.data_ptr()
             aligned = (base + 255) // 256 * 256
+            self.mem_offset = aligned - base  # the handle's buffers start here in self._mem
             self.h = fdlbm_create_ex(self.cfg, aligned, nbytes, stream)
         else:
             self.h = fdlbm_create_ex(self.cfg, None, 0, stream)
