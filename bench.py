@@ -6,16 +6,16 @@ A "step" is one time step of the whole method (moments -> f_eq -> Eq. 17 -> boun
 the workload's grid. The metric is GLUPS: site updates of all 33 velocities per second (nx*ny*steps/s).
 
 Default workload: the 4096 x 4096 four-quadrant Riemann problem (FP32 f, FP64 moments and f_eq,
-dx = 2.5e-4, dt = tau = 2.5e-6, lambda = 1, outflow on every side). Its f pair is 4.4 GB, far
+dx = 2.5e-4, dt = tau = 2.5e-6, lambda = 3, outflow on every side). Its f pair is 4.4 GB, far
 above the 129 MB L2, so no L2 flush is needed between steps.
 
 - value: device time over K steps from CUDA events on the solver's stream, with inputs already
   resident in HBM.
 - e2e: the public call sequence with pinned host buffers inside the timed region:
   fdlbm_set_macro (H2D), fdlbm_step(K), fdlbm_get_macro (D2H).
-- roofline: the fused step kernel against the FP64 pipe. Each FP64 instruction, FP32<->FP64
-  conversions included, issues at ~1.6 per clock per SM on this part, so the kernel is bound by
-  FP64 issue, not HBM. The HBM figures are reported beside it.
+- roofline: the fused step kernel against the FP64 pipe (2 FP64 instructions per clock per SM,
+  the nominal 1.25 TFLOP/s). FP64 on this part issues ~60x slower than FP32, so the kernel is
+  bound by FP64 issue, not HBM. The HBM figures are reported beside it.
 - cpu_baseline: the FP64 CPU oracle, timed on a bounded sample of the same workload.
 
 N > 1 (torchrun): every rank runs an independent replica with its own seed (weak scaling, no
@@ -34,13 +34,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic FP64-pipe operations per site update of the fused step (counted op by op; the
-# breakdown is in the design notes). FP32<->FP64 conversions issue on the FP64 pipe too.
-FP64_OPS_PER_LUP = {"fp64": 627, "fp32": 324}
+# FP64 arithmetic instructions (DADD + DFMA + DMUL) per site update of the fused step, without
+# the moments of the tile ring (ncu counts of the kernel minus that halo work; see profiles/).
+FP64_OPS_PER_LUP = {"fp64": 611, "fp32": 250}
 # Minimum HBM bytes per site update: read and write all 33 f once.
 BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4}
-# FP64 issue rate measured on this machine's GB300 (DFMA microbenchmark: 1.6 per clock per SM).
-FP64_OPS_PER_CLK_SM = 1.6
+# FP64 issue peak: 2 instructions per clock per SM, i.e. the nominal 1.25 TFLOP/s at 2.07 GHz
+# (ncu's pct-of-peak for the FP64 pipe agrees with it).
+FP64_OPS_PER_CLK_SM = 2.0
 N_SM = 152
 
 
@@ -267,7 +268,7 @@ def main():
                    "status": status, "parallelism": "replicas%d" % world},
         "roofline": {"bound": "alu", "kernel": "k_step (fused step)", "achieved": achieved,
                      "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak,
-                     "traffic": None, "peak_derivation": "1.6 FP64 ops/clk/SM (measured DFMA issue) x 152 SMs x %.0f MHz" % sm_mhz,
+                     "traffic": None, "peak_derivation": "2 FP64 ops/clk/SM (nominal 1.25 TFLOP/s) x 152 SMs x %.0f MHz sampled" % sm_mhz,
                      "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"), "peak_kind": peak_kind,
                              "frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0)}},
         "clocks": clocks,

@@ -19,7 +19,7 @@ Workloads (all FP64 macros, x fastest, m = 1 so rho = n and p = rho*T):
   reflection    steady regular reflection of Sec. 5.2 (Eq. 26): Mach-20 stream
                 (1, 20, 0, 0.5) entering on the left, top state (50/17, 16.7,
                 -5.71578, 22.61); Dirichlet left and top, outflow right, specular
-                wall at the bottom; lambda = 5. The paper gives no initial field;
+                wall at the bottom; lambda = 20, dt = tau = 0.0025 dx. The paper gives no initial field;
                 the domain starts in the top state and the incident shock forms at
                 the top-left corner (a sharp initial 30-degree shock is rejected by
                 the scheme within a few steps for every lambda tried).
@@ -116,13 +116,19 @@ REFLECTION_PRE = (1.0, 20.0, 0.0, 0.5)             # Eq. 26, left boundary
 REFLECTION_POST = (50.0 / 17.0, 16.7, -5.71578, 22.61)  # Eq. 26, top boundary
 
 
-def reflection(nx=1200, ny=300, dx=None, height=0.3, steps=10000, dt=1e-5, tau=1e-5, lam=5.0, init="post"):
+def reflection(nx=1200, ny=300, dx=None, height=0.3, steps=10000, dt=None, tau=None, lam=20.0, init="post"):
     """Steady regular reflection (Sec. 5.2, Eq. 26) on an nx x ny grid of height 0.3.
 
+    dt = tau = 0.0025 dx by default, so kappa_x = u dt/dx = 0.05 in the Mach-20 stream at every
+    resolution (2.5e-6 at dx = 1e-3; dt = 1e-5 there fails within 1000 steps for lambda up to 20).
     init="post": the whole domain starts in the top (post-shock) state; init="shock": post-shock
     above the incident-shock line y = height - x tan 30 deg, pre-shock below it."""
     if dx is None:
         dx = height / ny
+    if dt is None:
+        dt = 0.0025 * dx
+    if tau is None:
+        tau = dt
     x = (np.arange(nx) + 0.5) * dx
     y = (np.arange(ny) + 0.5) * dx
     X, Y = np.meshgrid(x, y)
