@@ -188,6 +188,55 @@ long fdlbm_steps_done(fdlbm_t h);
 /* Health bits (enum fdlbm_health_bits) accumulated since set_macro; synchronises. */
 unsigned fdlbm_health(fdlbm_t h);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batches: many solves advanced together, one kernel launch per time step over all members'
+ * tiles (replayed from a CUDA graph), for serving many small solves at once. Members keep their
+ * own buffers, grids, boundary kinds and states; they must share dx, dy, dt, tau, lambda, flags
+ * and the storage precision. A member's result is bitwise the same as when it is stepped alone
+ * with fdlbm_step (the per-node arithmetic is identical).
+ *
+ * While a solve is a member: fdlbm_step, fdlbm_set_macro(_device), fdlbm_set_f, fdlbm_load and
+ * fdlbm_autotune on it return FDLBM_E_STATE; read-out calls (get_macro, get_f, get_f_region,
+ * save, sync, health) first wait for the batch's stream. fdlbm_destroy removes it from its batch.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct fdlbm_batch_ctx* fdlbm_batch_t;
+
+/* cuda_stream: the batch's stream, or NULL for a stream the batch creates (graphs cannot be
+ * captured on the legacy default stream). */
+int fdlbm_batch_create(fdlbm_batch_t* out, void* cuda_stream);
+
+/* Add an initialised solve (synchronises the solve's own stream first). FDLBM_E_ARG if its
+ * scheme constants differ from the batch's, FDLBM_E_STATE if it is in a batch already, has no
+ * state, or carries a sticky error. */
+int fdlbm_batch_add(fdlbm_batch_t b, fdlbm_t h);
+
+/* Remove a member (synchronises the batch's stream). The solve keeps its state and step count. */
+int fdlbm_batch_remove(fdlbm_batch_t b, fdlbm_t h);
+
+/* Number of members, or a negative status. */
+int fdlbm_batch_size(fdlbm_batch_t b);
+
+/* Advance every member nsteps time steps (Eq. 17), asynchronously on the batch's stream.
+ * FDLBM_E_STATE if a member carries a sticky error (remove it first). */
+int fdlbm_batch_step(fdlbm_batch_t b, long nsteps);
+
+/* Wait for the batch and collect each member's health bits into its status: a member that saw
+ * a bad node (FDLBM_HEALTH_NUMERIC) gets the sticky FDLBM_E_NUMERIC. health (may be NULL)
+ * receives fdlbm_batch_size() words in member order (order of addition, removals closing the
+ * gaps). Returns the number of members carrying a sticky error (>= 0), or a negative status. */
+int fdlbm_batch_sync(fdlbm_batch_t b, unsigned* health);
+
+/* Launch variant of the batched step (as fdlbm_set_variant); the autotuner times every variant
+ * on the members' current states without advancing them. */
+int fdlbm_batch_set_variant(fdlbm_batch_t b, int variant);
+int fdlbm_batch_autotune(fdlbm_batch_t b, int trial_steps, float* times_ms);
+
+/* Release the batch (its members stay valid, detached). NULL-safe. */
+int fdlbm_batch_destroy(fdlbm_batch_t b);
+
+/* Message describing the last failure on b (NULL: as fdlbm_last_error(NULL)). Never NULL. */
+const char* fdlbm_batch_last_error(fdlbm_batch_t b);
+
 /* Largest nsteps one fdlbm_step_noalloc call accepts (its static scratch holds one word per step). */
 #define FDLBM_NOALLOC_MAX_STEPS 4096
 

@@ -64,8 +64,51 @@ def star_state(left, right, g=GAMMA, tol=1e-14, maxit=200):
     return p, u
 
 
+def vacuum_forms(left, right, g=GAMMA):
+    """True if the data separate into two rarefactions with vacuum between them:
+    2 (c_L + c_R)/(gamma - 1) <= u_R - u_L."""
+    cl = math.sqrt(g * left[2] / left[0])
+    cr = math.sqrt(g * right[2] / right[0])
+    return 2.0 * (cl + cr) / (g - 1.0) <= right[1] - left[1]
+
+
+def _sample_vacuum(left, right, xi, g):
+    """Two rarefactions fanning into vacuum: the left fan ends at u_L + 2 c_L/(gamma-1), the
+    right one begins at u_R - 2 c_R/(gamma-1); rho = p = 0 between them."""
+    rl, ul, pl = left
+    rr, ur, pr = right
+    cl = math.sqrt(g * pl / rl)
+    cr = math.sqrt(g * pr / rr)
+    sl_tail = ul + 2.0 * cl / (g - 1.0)
+    sr_tail = ur - 2.0 * cr / (g - 1.0)
+    xi = np.atleast_1d(np.asarray(xi, dtype=np.float64))
+    rho = np.zeros_like(xi)
+    u = np.zeros_like(xi)
+    p = np.zeros_like(xi)
+    for n, s in enumerate(xi):
+        if s <= ul - cl:
+            rho[n], u[n], p[n] = rl, ul, pl
+        elif s < sl_tail:
+            c = 2.0 / (g + 1.0) * (cl + 0.5 * (g - 1.0) * (ul - s))
+            rho[n] = rl * (c / cl) ** (2.0 / (g - 1.0))
+            u[n] = 2.0 / (g + 1.0) * (cl + 0.5 * (g - 1.0) * ul + s)
+            p[n] = pl * (c / cl) ** (2.0 * g / (g - 1.0))
+        elif s <= sr_tail:
+            rho[n], u[n], p[n] = 0.0, s, 0.0
+        elif s < ur + cr:
+            c = 2.0 / (g + 1.0) * (cr - 0.5 * (g - 1.0) * (ur - s))
+            rho[n] = rr * (c / cr) ** (2.0 / (g - 1.0))
+            u[n] = 2.0 / (g + 1.0) * (-cr + 0.5 * (g - 1.0) * ur + s)
+            p[n] = pr * (c / cr) ** (2.0 * g / (g - 1.0))
+        else:
+            rho[n], u[n], p[n] = rr, ur, pr
+    return rho, u, p
+
+
 def sample(left, right, xi, g=GAMMA):
     """(rho, u, p) arrays of the exact solution at similarity coordinates xi = (x - x0)/t."""
+    if vacuum_forms(left, right, g):
+        return _sample_vacuum(left, right, xi, g)
     rl, ul, pl = left
     rr, ur, pr = right
     ps, us = star_state(left, right, g)

@@ -10,6 +10,11 @@ cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Gr
                    : launch_step_f32(variant, f, fn, g, c, health, s);
 }
 
+cudaError_t launch_gather_health(const BatchMember* mem, int nmem, unsigned* out, cudaStream_t s) {
+  k_gather_health<<<(nmem + 127) / 128, 128, 0, s>>>(mem, nmem, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
                         const double* v, const double* T, cudaStream_t s) {
   dim3 b(32, 4);

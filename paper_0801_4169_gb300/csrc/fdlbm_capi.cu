@@ -14,33 +14,7 @@
 
 using namespace fdlbm;
 
-struct fdlbm_ctx {
-  fdlbm_config cfg;
-  Grid grid;
-  Coeffs coeffs;
-  size_t esize = 8;
-  size_t fbytes = 0;       // one distribution buffer (padded)
-  size_t total = 0;        // bytes of device memory in use
-  unsigned char* mem = nullptr;
-  bool owns_mem = false;
-  void* f[2] = {nullptr, nullptr};
-  int cur = 0;
-  unsigned* d_health = nullptr;
-  double* d_stage = nullptr;   // 4 * nx * ny doubles for host-pointer macro calls
-  double* d_fstage = nullptr;  // staging for get_f / set_f / get_f_region (allocated on first use)
-  size_t fstage_cap = 0;       // doubles
-  unsigned* h_health = nullptr;  // pinned
-  cudaStream_t stream = nullptr;
-  cudaEvent_t ev = nullptr;
-  bool ev_pending = false;
-  bool initialised = false;
-  long steps = 0;
-  int sticky = FDLBM_OK;
-  unsigned health = 0;
-  int variant = V_T32x8;
-  double bstate[4][4];
-  std::string err;
-};
+
 
 namespace {
 
@@ -352,12 +326,14 @@ int fdlbm_set_boundary_state(fdlbm_t h, int side, double rho, double u, double v
 }
 
 int fdlbm_set_macro_device(fdlbm_t h, const double* rho, const double* u, const double* v, const double* T) {
+  if (h && h->batch) return fail(h, FDLBM_E_STATE, "the solve is a member of a batch (step it with fdlbm_batch_step, or remove it first)");
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!rho || !u || !v || !T) return fail(h, FDLBM_E_ARG, "NULL macro array");
   return init_from_device_macros(h, rho, u, v, T);
 }
 
 int fdlbm_set_macro(fdlbm_t h, const double* rho, const double* u, const double* v, const double* T) {
+  if (h && h->batch) return fail(h, FDLBM_E_STATE, "the solve is a member of a batch (step it with fdlbm_batch_step, or remove it first)");
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!rho || !u || !v || !T) return fail(h, FDLBM_E_ARG, "NULL macro array");
   const size_t n = (size_t)h->cfg.nx * h->cfg.ny;
@@ -375,6 +351,7 @@ int fdlbm_set_macro(fdlbm_t h, const double* rho, const double* u, const double*
 }
 
 int fdlbm_step(fdlbm_t h, long nsteps) {
+  if (h && h->batch) return fail(h, FDLBM_E_STATE, "the solve is a member of a batch (step it with fdlbm_batch_step, or remove it first)");
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (nsteps < 0) return fail(h, FDLBM_E_ARG, "nsteps < 0");
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "fdlbm_step before fdlbm_set_macro / fdlbm_load");
@@ -393,6 +370,10 @@ int fdlbm_step(fdlbm_t h, long nsteps) {
 }
 
 int fdlbm_sync(fdlbm_t h) {
+  if (h && h->batch) {
+    cudaError_t fe = batch_fence(h->batch);
+    if (fe != cudaSuccess) return cuda_fail(h, fe, "batch fence");
+  }
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (h->initialised) {
     int rc = enqueue_health_copy(h);
@@ -405,6 +386,10 @@ int fdlbm_sync(fdlbm_t h) {
 }
 
 int fdlbm_get_macro_device(fdlbm_t h, double* rho, double* u, double* v, double* T) {
+  if (h && h->batch) {
+    cudaError_t fe = batch_fence(h->batch);
+    if (fe != cudaSuccess) return cuda_fail(h, fe, "batch fence");
+  }
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!rho || !u || !v || !T) return fail(h, FDLBM_E_ARG, "NULL macro array");
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "no state yet");
@@ -429,6 +414,10 @@ int fdlbm_get_macro(fdlbm_t h, double* rho, double* u, double* v, double* T) {
 }
 
 int fdlbm_get_f(fdlbm_t h, double* f) {
+  if (h && h->batch) {
+    cudaError_t fe = batch_fence(h->batch);
+    if (fe != cudaSuccess) return cuda_fail(h, fe, "batch fence");
+  }
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!f) return fail(h, FDLBM_E_ARG, "f is NULL");
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "no state yet");
@@ -443,6 +432,10 @@ int fdlbm_get_f(fdlbm_t h, double* f) {
 }
 
 int fdlbm_get_f_region(fdlbm_t h, int x0, int y0, int w, int hgt, double* f) {
+  if (h && h->batch) {
+    cudaError_t fe = batch_fence(h->batch);
+    if (fe != cudaSuccess) return cuda_fail(h, fe, "batch fence");
+  }
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!f) return fail(h, FDLBM_E_ARG, "f is NULL");
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "no state yet");
@@ -460,6 +453,7 @@ int fdlbm_get_f_region(fdlbm_t h, int x0, int y0, int w, int hgt, double* f) {
 }
 
 int fdlbm_set_f(fdlbm_t h, const double* f) {
+  if (h && h->batch) return fail(h, FDLBM_E_STATE, "the solve is a member of a batch (step it with fdlbm_batch_step, or remove it first)");
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!f) return fail(h, FDLBM_E_ARG, "f is NULL");
   int rc = ensure_fstage(h, full_f_doubles(h));
@@ -488,6 +482,10 @@ int fdlbm_set_f(fdlbm_t h, const double* f) {
 }
 
 int fdlbm_save(fdlbm_t h, const char* path) {
+  if (h && h->batch) {
+    cudaError_t fe = batch_fence(h->batch);
+    if (fe != cudaSuccess) return cuda_fail(h, fe, "batch fence");
+  }
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!path) return fail(h, FDLBM_E_ARG, "path is NULL");
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "no state yet");
@@ -530,6 +528,7 @@ int fdlbm_save(fdlbm_t h, const char* path) {
 }
 
 int fdlbm_load(fdlbm_t h, const char* path) {
+  if (h && h->batch) return fail(h, FDLBM_E_STATE, "the solve is a member of a batch (step it with fdlbm_batch_step, or remove it first)");
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!path) return fail(h, FDLBM_E_ARG, "path is NULL");
   FILE* fp = std::fopen(path, "rb");
@@ -589,6 +588,7 @@ int fdlbm_get_variant(fdlbm_t h) {
 }
 
 int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
+  if (h && h->batch) return fail(h, FDLBM_E_STATE, "the solve is a member of a batch (step it with fdlbm_batch_step, or remove it first)");
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (trial_steps < 1) return fail(h, FDLBM_E_ARG, "trial_steps must be >= 1");
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "autotune needs a state (set_macro first)");
@@ -632,6 +632,7 @@ unsigned fdlbm_health(fdlbm_t h) {
 
 int fdlbm_destroy(fdlbm_t h) {
   if (!h) return FDLBM_OK;
+  if (h->batch) fdlbm_batch_remove(h->batch, h);
   if (h->stream || h->mem) cudaStreamSynchronize(h->stream);
   if (h->owns_mem && h->mem) cudaFree(h->mem);
   if (h->d_fstage) cudaFree(h->d_fstage);

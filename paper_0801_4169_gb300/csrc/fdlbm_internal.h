@@ -10,6 +10,8 @@
 
 #include "../../include/fdlbm.h"
 
+struct fdlbm_batch_ctx;
+
 namespace fdlbm {
 
 constexpr int Q = 33;   // Watari-Tsutahara velocity count: rest + 4 speeds x 8 directions (Eq. 1)
@@ -59,6 +61,23 @@ struct Coeffs {
   float fr, fkx, fky, flam;
 };
 
+// One member of a batch (device-resident descriptor table, sorted by tile0).
+struct BatchMember {
+  Grid g;
+  void* f[2];                // the member's ping-pong buffers
+  unsigned* health;          // the member's health word
+  long long tile0;           // first block index of the member in the batched launch
+  int tiles_x;               // tiles along x (the tile shape is the batch's variant)
+  int cur0;                  // buffer holding the state at batch step 0 (parity)
+};
+
+// Tile shape (width, height) of a launch variant.
+inline void variant_tile(int v, int* tw, int* th) {
+  static const int W[8] = {32, 32, 32, 16, 64, 32, 32, 32}, H[8] = {4, 8, 16, 4, 8, 32, 16, 32};
+  *tw = W[v];
+  *th = H[v];
+}
+
 // Launch configuration of the fused step: tile of TW x TH nodes per CTA. Variants 0-5 cap the
 // registers at 128 per thread (2-4 CTAs per SM); the _R variants leave the allocation free
 // (one 256-thread CTA per SM, no spills).
@@ -73,6 +92,11 @@ cudaError_t launch_step_f64(int variant, const void* f, void* fn, const Grid& g,
                             cudaStream_t s);
 cudaError_t launch_step_f32(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                             cudaStream_t s);
+cudaError_t launch_batch_f64(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,
+                             const Coeffs& c, cudaStream_t s);
+cudaError_t launch_batch_f32(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,
+                             const Coeffs& c, cudaStream_t s);
+cudaError_t launch_gather_health(const BatchMember* mem, int nmem, unsigned* out, cudaStream_t s);
 cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
                         unsigned* health, cudaStream_t s);
 cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
@@ -96,5 +120,38 @@ Layout layout_of(const fdlbm_config* c);
 Coeffs make_coeffs(const fdlbm_config* cfg);
 int default_variant(const fdlbm_config* c);
 void set_thread_error(const char* msg);  // message returned by fdlbm_last_error(NULL)
+cudaError_t batch_fence(struct ::fdlbm_batch_ctx* b);  // wait for a batch's stream (fdlbm_batch.cu)
 
 }  // namespace fdlbm
+
+// A solve handle (opaque in the C ABI). Shared by the C ABI files.
+struct fdlbm_ctx {
+  fdlbm_config cfg;
+  fdlbm::Grid grid;
+  fdlbm::Coeffs coeffs;
+  size_t esize = 8;
+  size_t fbytes = 0;       // one distribution buffer (padded)
+  size_t total = 0;        // bytes of device memory in use
+  unsigned char* mem = nullptr;
+  bool owns_mem = false;
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  unsigned* d_health = nullptr;
+  double* d_stage = nullptr;   // 4 * nx * ny doubles for host-pointer macro calls
+  double* d_fstage = nullptr;  // staging for get_f / set_f / get_f_region (allocated on first use)
+  size_t fstage_cap = 0;       // doubles
+  unsigned* h_health = nullptr;  // pinned
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool ev_pending = false;
+  bool initialised = false;
+  long steps = 0;
+  int sticky = FDLBM_OK;
+  unsigned health = 0;
+  int variant = fdlbm::V_T32x8;
+  double bstate[4][4];
+  std::string err;
+  struct fdlbm_batch_ctx* batch = nullptr;  // the batch this solve is a member of, if any
+};
+
+

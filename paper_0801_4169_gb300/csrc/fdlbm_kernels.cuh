@@ -59,6 +59,26 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
   return __uint_as_float(t | (hi & 0x80000000u));
 }
 
+// 1/x for x in the FP32 normal range: an FP32 seed (relative error e ~ 2^-23) refined by one
+// third-order Newton step y (1 + e + e^2), e = 1 - x y, leaving O(e^3) ~ 2^-69: full FP64
+// accuracy up to the last-bit rounding, in 3 FMAs. Outside that range: IEEE division.
+__device__ __forceinline__ double rcp64(double x) {
+  const unsigned ah = (unsigned)__double2hiint(x) & 0x7fffffffu;
+  if (ah - (897u << 20) >= (252u << 20)) return 1.0 / x;
+  const double y = f32_to_f64_bits(__frcp_rn(f64_to_f32_rn(x)));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
+// Health tests on the bits (integer pipe): finite, and finite with x > 0.
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
+}
+__device__ __forceinline__ bool pos_finite_bits(double x) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  return hi >= 0 && hi < 0x7ff00000 && (hi | lo) != 0;
+}
+
 template <typename S>
 __device__ __forceinline__ S from_d(double x);
 template <>
@@ -138,6 +158,40 @@ __device__ __forceinline__ void store_node(S* __restrict__ fn, const Grid& g, in
         const bool wall = (c < 0 ? g.bc[2] : g.bc[3]) == BC_WALL;
         const int qq = wall ? mirror_y(QQ) : QQ;
         fn[(long long)qq * g.plane + (long long)(c + NG) * g.pitch + (gx + NG)] = val;
+      }
+    }
+  }
+}
+
+// Store the 8 directions of ring K at an interior node, then the ghost copies it owns.
+template <typename S, int K>
+__device__ __forceinline__ void store_ring(S* __restrict__ fn, const Grid& g, int gx, int gy, const GhostOwn& go,
+                                           const S (&v)[8]) {
+  const long long node = (long long)(gy + NG) * g.pitch + (gx + NG);
+#pragma unroll
+  for (int d = 0; d < 8; ++d) fn[(long long)(1 + 8 * K + d) * g.plane + node] = v[d];
+  if (go.mx | go.my) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (go.mx & (1u << t)) {
+        const int c = ghost_coord(t, g.nx);
+        const bool wall = (c < 0 ? g.bc[0] : g.bc[1]) == BC_WALL;
+        const long long gn = (long long)(gy + NG) * g.pitch + (c + NG);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          const int q = 1 + 8 * K + d;
+          fn[(long long)(wall ? mirror_x(q) : q) * g.plane + gn] = v[d];
+        }
+      }
+      if (go.my & (1u << t)) {
+        const int c = ghost_coord(t, g.ny);
+        const bool wall = (c < 0 ? g.bc[2] : g.bc[3]) == BC_WALL;
+        const long long gn = (long long)(c + NG) * g.pitch + (gx + NG);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          const int q = 1 + 8 * K + d;
+          fn[(long long)(wall ? mirror_y(q) : q) * g.plane + gn] = v[d];
+        }
       }
     }
   }
@@ -229,20 +283,19 @@ struct Macro {
 };
 __device__ __forceinline__ Macro to_macro(const Mom& m) {
   Macro o;
-  const double in = 1.0 / m.n;
+  const double in = rcp64(m.n);
   o.n = m.n;
   o.ux = m.jx * in;
   o.uy = m.jy * in;
   const double u2 = fma(o.ux, o.ux, o.uy * o.uy);
-  o.T = fma(0.5 * m.e2, in, -0.5 * u2);
+  o.T = 0.5 * fma(m.e2, in, -u2);
   o.P = m.n * o.T;
   return o;
 }
 
 __device__ __forceinline__ bool macro_ok(const Macro& o) {
   // finite, n > 0, T > 0 (so P > 0 and the switch denominator of Eq. 16 is positive)
-  return (o.n > 0.0) && (o.T > 0.0) && isfinite(o.n) && isfinite(o.ux) && isfinite(o.uy) && isfinite(o.T) &&
-         (o.n < INFINITY) && (o.T < INFINITY);
+  return pos_finite_bits(o.n) && pos_finite_bits(o.T) && finite_bits(o.ux) && finite_bits(o.uy);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -258,7 +311,7 @@ struct EqSite {
 __device__ __forceinline__ EqSite eq_site(double n, double ux, double uy, double T, const Coeffs& c) {
   EqSite e;
   const double th = T;  // theta = T/m, m = 1
-  const double ith = 1.0 / th;
+  const double ith = rcp64(th);
   const double px = ux * ith, py = uy * ith;
   e.p[0] = px;
   e.p[1] = kS * (px + py);
@@ -295,12 +348,33 @@ __device__ __forceinline__ EqRing eq_ring(const EqSite& e, int k, const Coeffs& 
   r.ep = nF * c.v3_6[k];
   return r;
 }
-// r f_eq for the direction with projection p and its opposite
+// r f_eq for the direction with projection p and its opposite, from the even part
+// NE = alpha + x (beta + gamma x) and the odd part NO = p (delta + eps x), both in FP64. The
+// FP64 path forms NE +- NO in FP64; the FP32-storage path rounds NE and NO to FP32 and forms
+// the pair there, the precision the sum is stored in.
+__device__ __forceinline__ void eq_parts(const EqRing& r, double p, double x, double& NE, double& NO) {
+  NE = fma(x, fma(r.ga, x, r.be), r.al);
+  NO = p * fma(r.ep, x, r.de);
+}
 __device__ __forceinline__ void eq_pair(const EqRing& r, double p, double x, double& fp, double& fm) {
-  const double NE = fma(x, fma(r.ga, x, r.be), r.al);
-  const double NO = p * fma(r.ep, x, r.de);
+  double NE, NO;
+  eq_parts(r, p, x, NE, NO);
   fp = NE + NO;
   fm = NE - NO;
+}
+template <typename S>
+__device__ __forceinline__ void eq_pair_s(const EqRing& r, double p, double x, S& fp, S& fm);
+template <>
+__device__ __forceinline__ void eq_pair_s<double>(const EqRing& r, double p, double x, double& fp, double& fm) {
+  eq_pair(r, p, x, fp, fm);
+}
+template <>
+__device__ __forceinline__ void eq_pair_s<float>(const EqRing& r, double p, double x, float& fp, float& fm) {
+  double NE, NO;
+  eq_parts(r, p, x, NE, NO);
+  const float e = f64_to_f32_rn(NE), o = f64_to_f32_rn(NO);
+  fp = e + o;
+  fm = e - o;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -393,42 +467,42 @@ __device__ __forceinline__ void update_ring(const S* __restrict__ f, S* __restri
   w.nu[1] = nuy;
   const EqRing er = eq_ring(e, K, c);
   const S* fq = f + off;
-  double fp, fm;
+  // All 8 directions of the ring are computed before any store, so the ring is one basic block
+  // the compiler can interleave (the ghost-copy branch comes once per ring, not per velocity).
+  S out[8], fp, fm;
   // pair (d7: 0 deg, d3: 180 deg), projection p_x
-  eq_pair(er, e.p[0], e.x[0], fp, fm);
-  store_node<S, 1 + 8 * K + 7>(fn, g, gx, gy, go,
-                               stencil_dir<S, 7>(fq + (long long)(1 + 8 * K + 7) * g.plane, g.pitch, w, from_d<S>(fp)));
-  store_node<S, 1 + 8 * K + 3>(fn, g, gx, gy, go,
-                               stencil_dir<S, 3>(fq + (long long)(1 + 8 * K + 3) * g.plane, g.pitch, w, from_d<S>(fm)));
+  eq_pair_s<S>(er, e.p[0], e.x[0], fp, fm);
+  out[7] = stencil_dir<S, 7>(fq + (long long)(1 + 8 * K + 7) * g.plane, g.pitch, w, fp);
+  out[3] = stencil_dir<S, 3>(fq + (long long)(1 + 8 * K + 3) * g.plane, g.pitch, w, fm);
   // pair (d0: 45 deg, d4: 225 deg), projection s(p_x + p_y)
-  eq_pair(er, e.p[1], e.x[1], fp, fm);
-  store_node<S, 1 + 8 * K + 0>(fn, g, gx, gy, go,
-                               stencil_dir<S, 0>(fq + (long long)(1 + 8 * K + 0) * g.plane, g.pitch, w, from_d<S>(fp)));
-  store_node<S, 1 + 8 * K + 4>(fn, g, gx, gy, go,
-                               stencil_dir<S, 4>(fq + (long long)(1 + 8 * K + 4) * g.plane, g.pitch, w, from_d<S>(fm)));
+  eq_pair_s<S>(er, e.p[1], e.x[1], fp, fm);
+  out[0] = stencil_dir<S, 0>(fq + (long long)(1 + 8 * K + 0) * g.plane, g.pitch, w, fp);
+  out[4] = stencil_dir<S, 4>(fq + (long long)(1 + 8 * K + 4) * g.plane, g.pitch, w, fm);
   // pair (d1: 90 deg, d5: 270 deg), projection p_y
-  eq_pair(er, e.p[2], e.x[2], fp, fm);
-  store_node<S, 1 + 8 * K + 1>(fn, g, gx, gy, go,
-                               stencil_dir<S, 1>(fq + (long long)(1 + 8 * K + 1) * g.plane, g.pitch, w, from_d<S>(fp)));
-  store_node<S, 1 + 8 * K + 5>(fn, g, gx, gy, go,
-                               stencil_dir<S, 5>(fq + (long long)(1 + 8 * K + 5) * g.plane, g.pitch, w, from_d<S>(fm)));
+  eq_pair_s<S>(er, e.p[2], e.x[2], fp, fm);
+  out[1] = stencil_dir<S, 1>(fq + (long long)(1 + 8 * K + 1) * g.plane, g.pitch, w, fp);
+  out[5] = stencil_dir<S, 5>(fq + (long long)(1 + 8 * K + 5) * g.plane, g.pitch, w, fm);
   // pair (d2: 135 deg, d6: 315 deg), projection s(p_y - p_x)
-  eq_pair(er, e.p[3], e.x[3], fp, fm);
-  store_node<S, 1 + 8 * K + 2>(fn, g, gx, gy, go,
-                               stencil_dir<S, 2>(fq + (long long)(1 + 8 * K + 2) * g.plane, g.pitch, w, from_d<S>(fp)));
-  store_node<S, 1 + 8 * K + 6>(fn, g, gx, gy, go,
-                               stencil_dir<S, 6>(fq + (long long)(1 + 8 * K + 6) * g.plane, g.pitch, w, from_d<S>(fm)));
+  eq_pair_s<S>(er, e.p[3], e.x[3], fp, fm);
+  out[2] = stencil_dir<S, 2>(fq + (long long)(1 + 8 * K + 2) * g.plane, g.pitch, w, fp);
+  out[6] = stencil_dir<S, 6>(fq + (long long)(1 + 8 * K + 6) * g.plane, g.pitch, w, fm);
+  store_ring<S, K>(fn, g, gx, gy, go, out);
 }
 
 template <typename S>
 __device__ __forceinline__ S to_s(double x) { return from_d<S>(x); }
 
+__device__ __forceinline__ double recip(double x) { return rcp64(x); }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+
 // ---------------------------------------------------------------------------------------------
 // The fused step. CTA = BX x BY threads; tile TW x TH = BX x (BY*RY) nodes. Shared memory holds
 // n, ux, uy, T, P of the tile and its 1-node ring (corners excluded), computed once per node.
-template <typename S, int BX, int BY, int RY, int MINB>
-__global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f, S* __restrict__ fn, Grid g, Coeffs c,
-                                                  unsigned* __restrict__ health) {
+// One tile (tx, ty) of one solve: the body shared by the single-solve kernel (k_step) and the
+// batched kernel (k_step_batch), so a node's arithmetic is the same alone and in a batch.
+template <typename S, int BX, int BY, int RY>
+__device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict__ fn, const Grid& g, const Coeffs& c,
+                                          unsigned* __restrict__ health, int tx, int ty) {
   constexpr int TW = BX, TH = BY * RY, SW = TW + 2, SH = TH + 2, NT = BX * BY;
   using SC = StencilConsts<S>;
   // P is staged in the storage precision: the switch of Eq. 16 is a limiter coefficient, and in
@@ -436,7 +510,7 @@ __global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f,
   __shared__ double s_n[SH][SW], s_ux[SH][SW], s_uy[SH][SW], s_T[SH][SW];
   __shared__ S s_P[SH][SW];
   const int tid = threadIdx.y * BX + threadIdx.x;
-  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+  const int x0 = tx * TW, y0 = ty * TH;
   unsigned bits = 0;
 
   // Phase 1: moments on the tile and its ring (needed: interior nodes and the ghost layer next
@@ -473,8 +547,8 @@ __global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f,
     } else {
       const S P0 = s_P[ly][lx];
       const S sx = s_P[ly][lx + 1] + s_P[ly][lx - 1], sy = s_P[ly + 1][lx] + s_P[ly - 1][lx];
-      thx = SC::lam(c) * fabs(fma((S)-2, P0, sx) / fma((S)2, P0, sx));
-      thy = SC::lam(c) * fabs(fma((S)-2, P0, sy) / fma((S)2, P0, sy));
+      thx = SC::lam(c) * fabs(fma((S)-2, P0, sx) * recip(fma((S)2, P0, sx)));
+      thy = SC::lam(c) * fabs(fma((S)-2, P0, sy) * recip(fma((S)2, P0, sy)));
     }
     const S akx = fabs(from_d<S>(ux) * SC::kx(c)), aky = fabs(from_d<S>(uy) * SC::ky(c));
     if (akx > (S)1 || aky > (S)1) bits |= H_KAPPA;
@@ -502,6 +576,46 @@ __global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f,
     update_ring<S, 3>(f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
   }
   if (bits) atomicOr(health, bits);
+}
+
+template <typename S, int BX, int BY, int RY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f, S* __restrict__ fn, Grid g, Coeffs c,
+                                                  unsigned* __restrict__ health) {
+  step_tile<S, BX, BY, RY>(f, fn, g, c, health, blockIdx.x, blockIdx.y);
+}
+
+// Batched step: every member solve of a batch advances one time step in one launch. Members share
+// the scheme constants (dx, dy, dt, tau, lambda, flags, precision), not their grids, boundaries or
+// buffers. Block b runs tile (b - tile0) of the member whose [tile0, tile0 + tiles) holds b.
+template <typename S, int BX, int BY, int RY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB) k_step_batch(const BatchMember* __restrict__ mem, int nmem,
+                                                        unsigned long long step, Coeffs c) {
+  __shared__ int s_sel;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = nmem - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (mem[mid].tile0 <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_sel = lo;
+  }
+  __syncthreads();
+  const BatchMember& m = mem[s_sel];
+  const Grid g = m.g;
+  const long long local = (long long)blockIdx.x - m.tile0;
+  const int tx = (int)(local % m.tiles_x), ty = (int)(local / m.tiles_x);
+  const int par = (int)((m.cur0 + step) & 1ull);
+  const S* in = static_cast<const S*>(m.f[par]);
+  S* out = static_cast<S*>(m.f[par ^ 1]);
+  step_tile<S, BX, BY, RY>(in, out, g, c, m.health, tx, ty);
+}
+
+// health words of the members into one array (one device-to-host copy per batch round)
+__global__ void k_gather_health(const BatchMember* __restrict__ mem, int nmem, unsigned* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nmem) out[i] = *mem[i].health;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -627,6 +741,29 @@ cudaError_t launch_step_t(const void* f, void* fn, const Grid& g, const Coeffs& 
   dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY * RY - 1) / (BY * RY));
   k_step<S, BX, BY, RY, MINB><<<grid, block, 0, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g, c, health);
   return cudaGetLastError();
+}
+
+template <typename S, int BX, int BY, int RY, int MINB>
+cudaError_t launch_batch_t(const BatchMember* mem, int nmem, long long tiles, unsigned long long step, const Coeffs& c,
+                           cudaStream_t s) {
+  k_step_batch<S, BX, BY, RY, MINB><<<dim3((unsigned)tiles), dim3(BX, BY), 0, s>>>(mem, nmem, step, c);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_batch_v(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,
+                           const Coeffs& c, cudaStream_t s) {
+  switch (variant) {
+    case V_T32x4: return launch_batch_t<S, 32, 4, 1, 4>(mem, nmem, tiles, step, c, s);
+    case V_T32x8: return launch_batch_t<S, 32, 4, 2, 4>(mem, nmem, tiles, step, c, s);
+    case V_T32x16: return launch_batch_t<S, 32, 8, 2, 2>(mem, nmem, tiles, step, c, s);
+    case V_T16x4: return launch_batch_t<S, 16, 4, 1, 1>(mem, nmem, tiles, step, c, s);
+    case V_T64x8: return launch_batch_t<S, 64, 4, 2, 2>(mem, nmem, tiles, step, c, s);
+    case V_T32x32: return launch_batch_t<S, 32, 8, 4, 2>(mem, nmem, tiles, step, c, s);
+    case V_T32x16_R: return launch_batch_t<S, 32, 8, 2, 1>(mem, nmem, tiles, step, c, s);
+    case V_T32x32_R: return launch_batch_t<S, 32, 8, 4, 1>(mem, nmem, tiles, step, c, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename S>

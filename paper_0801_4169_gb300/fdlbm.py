@@ -83,6 +83,16 @@ def lib():
             "fdlbm_last_error": (ctypes.c_char_p, [_VP]),
             "fdlbm_version": (ctypes.c_char_p, []),
             "fdlbm_step_noalloc": (ctypes.c_int, [cfgp, _VP, _VP, ctypes.c_long, ctypes.POINTER(ctypes.c_long), _VP]),
+            "fdlbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP]),
+            "fdlbm_batch_add": (ctypes.c_int, [_VP, _VP]),
+            "fdlbm_batch_remove": (ctypes.c_int, [_VP, _VP]),
+            "fdlbm_batch_size": (ctypes.c_int, [_VP]),
+            "fdlbm_batch_step": (ctypes.c_int, [_VP, ctypes.c_long]),
+            "fdlbm_batch_sync": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint)]),
+            "fdlbm_batch_set_variant": (ctypes.c_int, [_VP, ctypes.c_int]),
+            "fdlbm_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
+            "fdlbm_batch_destroy": (ctypes.c_int, [_VP]),
+            "fdlbm_batch_last_error": (ctypes.c_char_p, [_VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -249,6 +259,62 @@ def fdlbm_destroy(h):
 
 def fdlbm_last_error(h):
     s = lib().fdlbm_last_error(h)
+    return s.decode() if s else ""
+
+
+def _bcheck(b, rc):
+    if rc < 0:
+        raise FdlbmError(rc, fdlbm_batch_last_error(b))
+    return rc
+
+
+def fdlbm_batch_create(stream=None):
+    b = _VP()
+    _bcheck(None, lib().fdlbm_batch_create(ctypes.byref(b), _stream_ptr(stream)))
+    return b.value
+
+
+def fdlbm_batch_add(b, h):
+    return _bcheck(b, lib().fdlbm_batch_add(b, h))
+
+
+def fdlbm_batch_remove(b, h):
+    return _bcheck(b, lib().fdlbm_batch_remove(b, h))
+
+
+def fdlbm_batch_size(b):
+    return _bcheck(b, lib().fdlbm_batch_size(b))
+
+
+def fdlbm_batch_step(b, nsteps):
+    return _bcheck(b, lib().fdlbm_batch_step(b, int(nsteps)))
+
+
+def fdlbm_batch_sync(b):
+    """Returns (number of members with a sticky error, per-member health words)."""
+    n = max(1, fdlbm_batch_size(b))
+    words = (ctypes.c_uint * n)()
+    failed = _bcheck(b, lib().fdlbm_batch_sync(b, words))
+    return failed, list(words)[:fdlbm_batch_size(b)]
+
+
+def fdlbm_batch_set_variant(b, variant):
+    return _bcheck(b, lib().fdlbm_batch_set_variant(b, int(variant)))
+
+
+def fdlbm_batch_autotune(b, trial_steps=3):
+    n = fdlbm_variant_count()
+    times = (ctypes.c_float * n)()
+    _bcheck(b, lib().fdlbm_batch_autotune(b, int(trial_steps), times))
+    return list(times)
+
+
+def fdlbm_batch_destroy(b):
+    return lib().fdlbm_batch_destroy(b)
+
+
+def fdlbm_batch_last_error(b):
+    s = lib().fdlbm_batch_last_error(b)
     return s.decode() if s else ""
 
 

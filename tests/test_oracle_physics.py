@@ -177,3 +177,19 @@ def test_mach20_into_rest_is_rejected_by_the_scheme():
         s.set_macro(*w.macros())
         assert s.step(1) == 0
         assert s.step(1) == -4
+
+
+def test_vacuum_solution_is_continuous_and_satisfies_riemann_invariants():
+    """Sjogreen data (Eq. 23) with the model's gamma = 2 separate into vacuum (2(c_L + c_R)/(gamma-1)
+    = 3.58 < u_R - u_L = 4). The sampled fans are continuous, reach rho = 0 at their tails, and keep
+    the Riemann invariant u + 2c/(gamma-1) (left fan) constant."""
+    L, R = (1.0, -2.0, 0.4), (1.0, 2.0, 0.4)
+    assert riemann.vacuum_forms(L, R) and not riemann.vacuum_forms(L, R, g=1.4)
+    xi = np.linspace(-4.0, 4.0, 4001)
+    rho, u, p = riemann.sample(L, R, xi)
+    assert np.all(rho >= 0) and np.max(np.abs(np.diff(rho))) < 0.01
+    c = np.sqrt(2.0 * np.maximum(p, 0) / np.maximum(rho, 1e-300))
+    fan = (xi > -2.0 - math.sqrt(0.8) + 1e-3) & (xi < -2.0 + 2 * math.sqrt(0.8) - 1e-3)
+    inv = u[fan] + 2.0 * c[fan] / (2.0 - 1.0)
+    assert np.max(np.abs(inv - (-2.0 + 2.0 * math.sqrt(0.8)))) < 1e-9
+    assert rho[np.argmin(np.abs(xi))] == 0.0
