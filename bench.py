@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 # FP64 arithmetic instructions (DADD + DFMA + DMUL) per site update of the fused step, without
 # the moments of the tile ring (ncu counts of the kernel minus that halo work; see profiles/).
-FP64_OPS_PER_LUP = {"fp64": 611, "fp32": 250}
+FP64_OPS_PER_LUP = {"fp64": 579, "fp32": 228}
 # Minimum HBM bytes per site update: read and write all 33 f once.
 BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4}
 # FP64 issue peak: 2 instructions per clock per SM, i.e. the nominal 1.25 TFLOP/s at 2.07 GHz
@@ -114,6 +114,19 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def aggregate_over_ranks(ms_local, lups_local, dist=None, device=None):
+    """Weak-scaling aggregation across replicas: the job's time is the slowest rank's, its work the
+    sum over ranks. Works with any torch.distributed backend (NCCL on GPUs, gloo in the CPU tests)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(lups_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return ms, float(w.item()), float(w.item()) / (ms * 1e-3) / 1e9
 
 
 def oracle_sample(name, budget_s=20.0):
@@ -223,13 +236,10 @@ def main():
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     status = solver.sync()
-    ms_t = torch.tensor([ms], device="cuda")
+    lups = w.nx * w.ny * args.steps
     if dist:
         dist.barrier()
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    lups = w.nx * w.ny * args.steps
-    glups = lups * world / (ms_max * 1e-3) / 1e9
+    ms_max, lups_all, glups = aggregate_over_ranks(ms, lups, dist, device="cuda")
     per_launch_ms = ms / args.steps
 
     # end-to-end: the public API with pinned host buffers, copies inside the timed region
@@ -242,10 +252,7 @@ def main():
     solver.step(args.steps)
     rc = F.lib().fdlbm_get_macro(solver.h, *[F._hp(a) for a in h_out])
     t_e2e = time.perf_counter() - t0
-    t_e2e_t = torch.tensor([t_e2e], device="cuda")
-    if dist:
-        dist.all_reduce(t_e2e_t, op=dist.ReduceOp.MAX)
-    e2e_glups = lups * world / float(t_e2e_t.item()) / 1e9
+    _, _, e2e_glups = aggregate_over_ranks(t_e2e * 1e3, lups, dist, device="cuda")
     macro_bytes = 4 * w.nx * w.ny * 8
 
     peaks, peak_kind = load_peaks()

@@ -237,6 +237,70 @@ int fdlbm_batch_destroy(fdlbm_batch_t b);
 /* Message describing the last failure on b (NULL: as fdlbm_last_error(NULL)). Never NULL. */
 const char* fdlbm_batch_last_error(fdlbm_batch_t b);
 
+/* ---------------------------------------------------------------------------------------------
+ * Serving: a continuous-batching runtime. A worker thread owns all device work. Clients submit
+ * solves from any thread, then poll, wait and collect results. Each round the worker:
+ *  - admits queued requests in submission order while the HBM budget and slots allow;
+ *  - advances every admitted solve by the same number of steps, one batch per group of solves
+ *    sharing scheme constants and precision;
+ *  - retires finished solves (moments read back to host memory) and failed ones.
+ * A numerical failure of an FP32-storage solve is reported; it is never re-run in FP64.
+ * Time to solution runs from submission to retirement.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct fdlbm_server_ctx* fdlbm_server_t;
+
+enum fdlbm_req_status { FDLBM_REQ_QUEUED = 0, FDLBM_REQ_ACTIVE = 1, FDLBM_REQ_DONE = 2, FDLBM_REQ_FAILED = 3,
+                        FDLBM_REQ_CANCELLED = 4 };
+
+/* FDLBM_ENGINE_GPU runs the solves in batches (one launch per step per group).
+ * FDLBM_ENGINE_GPU_SEPARATE runs the same scheduler but steps every solve with its own launches
+ * (the unbatched baseline). FDLBM_ENGINE_SIMULATED runs the scheduler with no device work: each
+ * step sleeps 1 ns per site, and results are filled with the step count. It is for testing the
+ * scheduling policy on machines without a GPU. */
+enum fdlbm_engine { FDLBM_ENGINE_GPU = 0, FDLBM_ENGINE_SIMULATED = 1, FDLBM_ENGINE_GPU_SEPARATE = 2 };
+
+typedef struct {
+  fdlbm_config cfg;                 /* the solve (as fdlbm_create_ex) */
+  double bstate[4][4];              /* Dirichlet states (rho, u, v, T) per side */
+  const double *rho, *u, *v, *T;    /* initial macros, nx*ny each, x fastest; copied by submit */
+  long steps;                       /* time steps to run (>= 0) */
+  long sim_fail_step;               /* simulated engine only: fail on reaching this step (0: never) */
+} fdlbm_request;
+
+typedef struct {
+  long long submitted, done, failed, queued, rounds;
+  int max_active;                   /* most solves on the device at once */
+  size_t max_bytes;                 /* most device bytes in use at once (<= budget) */
+  double p50_s, p99_s, mean_s;      /* time to solution of finished requests */
+  double wall_s;                    /* first submission to last retirement */
+  double aggregate_glups;           /* site updates of all solves / wall_s */
+} fdlbm_server_stats_t;
+
+/* budget_bytes: device memory the admitted solves may hold together (fdlbm_device_bytes each);
+ * max_slots: most solves at once; round_steps: most steps per round; cuda_stream: the server's
+ * stream or NULL (one is created). The GPU engine uses the device current at the call. */
+int fdlbm_server_create(fdlbm_server_t* out, size_t budget_bytes, int max_slots, long round_steps, int engine,
+                        void* cuda_stream);
+/* Thread-safe. Copies the request's arrays; *id identifies it. A request larger than the budget
+ * fails at once (status FDLBM_REQ_FAILED). */
+int fdlbm_server_submit(fdlbm_server_t s, const fdlbm_request* req, long long* id);
+int fdlbm_server_poll(fdlbm_server_t s, long long id, int* status);
+/* Wait until the request is DONE, FAILED or CANCELLED (timeout_s < 0: no limit). FDLBM_E_TIMEOUT
+ * if the time ran out first. */
+int fdlbm_server_wait(fdlbm_server_t s, long long id, double timeout_s, int* status);
+/* Collect a finished request's moments (any array may be NULL) and its time to solution, and
+ * release it. A failed request returns its error code (FDLBM_E_NUMERIC for a numerical failure,
+ * FDLBM_E_OOM if it exceeds the budget or could not be allocated) and is released;
+ * FDLBM_E_STATE if it is still queued or active. */
+int fdlbm_server_result(fdlbm_server_t s, long long id, double* rho, double* u, double* v, double* T,
+                        double* seconds_to_solution);
+int fdlbm_server_stats(fdlbm_server_t s, fdlbm_server_stats_t* st);
+/* Stop the worker after its current round; queued and active requests become CANCELLED.
+ * NULL-safe. */
+int fdlbm_server_destroy(fdlbm_server_t s);
+/* Message of the last failure on s (valid until the next call on s). */
+const char* fdlbm_server_last_error(fdlbm_server_t s);
+
 /* Largest nsteps one fdlbm_step_noalloc call accepts (its static scratch holds one word per step). */
 #define FDLBM_NOALLOC_MAX_STEPS 4096
 

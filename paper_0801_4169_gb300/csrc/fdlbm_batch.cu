@@ -24,6 +24,7 @@ struct fdlbm_batch_ctx {
   fdlbm_config scheme;                 // scheme constants shared by the members
   Coeffs coeffs;
   int variant = V_T32x8;
+  bool variant_set = false;            // set explicitly or by the autotuner; else from the members
   bool dirty = true;                   // descriptor table / graph out of date
   BatchMember* d_table = nullptr;
   size_t table_cap = 0;
@@ -70,6 +71,11 @@ cudaError_t launch_one(fdlbm_batch_ctx* b, unsigned long long step) {
 int rebuild(fdlbm_batch_ctx* b) {
   drop_graph(b);
   const size_t n = b->members.size();
+  if (!b->variant_set && n) {  // tile height from the tallest member (thin shock tubes: 4 rows)
+    int ny = 0;
+    for (fdlbm_ctx* h : b->members) ny = std::max(ny, h->cfg.ny);
+    b->variant = ny <= 4 ? V_T32x4 : ny <= 8 ? V_T32x8 : V_T32x16;
+  }
   b->host_table.resize(n);
   int tw, th;
   variant_tile(b->variant, &tw, &th);
@@ -284,7 +290,8 @@ int fdlbm_batch_sync(fdlbm_batch_t b, unsigned* health) {
 
 int fdlbm_batch_set_variant(fdlbm_batch_t b, int variant) {
   if (!b) return bfail(nullptr, FDLBM_E_ARG, "batch is NULL");
-  if (variant < 0 || variant >= V_COUNT) return bfail(b, FDLBM_E_ARG, "variant out of range");
+  if (variant < 0 || variant >= V_TILE_COUNT) return bfail(b, FDLBM_E_ARG, "variant out of range for a batch");
+  b->variant_set = true;
   if (variant != b->variant) {
     b->variant = variant;
     b->dirty = true;
@@ -303,7 +310,12 @@ int fdlbm_batch_autotune(fdlbm_batch_t b, int trial_steps, float* times_ms) {
   int best = b->variant;
   float best_ms = 1e30f;
   for (int v = 0; v < V_COUNT && e == cudaSuccess; ++v) {
+    if (v >= V_TILE_COUNT) {  // ring-parallel variants are single-solve only
+      if (times_ms) times_ms[v] = 0.f;
+      continue;
+    }
     b->variant = v;
+    b->variant_set = true;
     int rc = rebuild(b);
     if (rc) {
       cudaEventDestroy(a0);
@@ -330,6 +342,7 @@ int fdlbm_batch_autotune(fdlbm_batch_t b, int trial_steps, float* times_ms) {
   cudaEventDestroy(a1);
   if (e != cudaSuccess) return bcuda(b, e, "batch autotune");
   b->variant = best;
+  b->variant_set = true;
   b->dirty = true;
   return FDLBM_OK;
 }

@@ -137,6 +137,7 @@ Coeffs make_coeffs(const fdlbm_config* cfg) {
 
 int default_variant(const fdlbm_config* c) {
   const long long sites = (long long)c->nx * c->ny;
+  if (sites <= 65536) return V_RP16x4;  // small grids: latency-bound, four lanes per node
   if (c->ny <= 4) return V_T32x4;
   if (sites < 200000) return V_T32x8;
   return V_T32x16;

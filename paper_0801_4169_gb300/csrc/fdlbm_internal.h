@@ -81,9 +81,11 @@ inline void variant_tile(int v, int* tw, int* th) {
 // Launch configuration of the fused step: tile of TW x TH nodes per CTA. Variants 0-5 cap the
 // registers at 128 per thread (2-4 CTAs per SM); the _R variants leave the allocation free
 // (one 256-thread CTA per SM, no spills).
+// V_RP* are the ring-parallel variants (four lanes per node) for small grids; batches use the
+// tile variants only (V_TILE_COUNT).
 enum StepVariant {
   V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_T32x32 = 5, V_T32x16_R = 6,
-  V_T32x32_R = 7, V_COUNT = 8
+  V_T32x32_R = 7, V_TILE_COUNT = 8, V_RP16x4 = 8, V_RP8x4 = 9, V_COUNT = 10
 };
 
 // Kernel launchers (fdlbm_aux.cu, fdlbm_step_f32.cu, fdlbm_step_f64.cu). All return

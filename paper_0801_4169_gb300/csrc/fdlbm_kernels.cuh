@@ -164,8 +164,8 @@ __device__ __forceinline__ void store_node(S* __restrict__ fn, const Grid& g, in
 }
 
 // Store the 8 directions of ring K at an interior node, then the ghost copies it owns.
-template <typename S, int K>
-__device__ __forceinline__ void store_ring(S* __restrict__ fn, const Grid& g, int gx, int gy, const GhostOwn& go,
+template <typename S>
+__device__ __forceinline__ void store_ring(S* __restrict__ fn, const Grid& g, int gx, int gy, const GhostOwn& go, int K,
                                            const S (&v)[8]) {
   const long long node = (long long)(gy + NG) * g.pitch + (gx + NG);
 #pragma unroll
@@ -206,42 +206,64 @@ __device__ __forceinline__ GhostOwn ghost_own(const Grid& g, int gx, int gy) {
 
 // ---------------------------------------------------------------------------------------------
 // Moments of Eqs. 3-5 (FP64). One ring of 8 values g[d]:
-//   S = sum g,  X = (g7 - g3) + s((g0 - g4) + (g6 - g2)),  Y = (g1 - g5) + s((g0 - g4) - (g6 - g2))
-// with n += S, j_x += v X, j_y += v Y, sum |v|^2 f += v^2 S.
+//   S = sum g,  X = (g7 - g3) + s((g0 - g4) + (g6 - g2)),  Y = (g1 - g5) + s((g0 - g4) - (g6 - g2)),
+// and the rings combine pairwise, (ring 0 + ring 1) + (ring 2 + ring 3):
+//   n  = ((f_0 + S_0) + S_1) + (S_2 + S_3)
+//   jx = fma(v_0, X_0, v_1 X_1) + fma(v_2, X_2, v_3 X_3)      (jy with Y; sum |v|^2 f with v^2, S)
+// The tree is fixed so that the ring-parallel kernel, whose four lanes hold one ring each, forms
+// exactly the same sums with two shuffle stages as the kernels that hold all rings in one thread.
 struct Mom {
   double n, jx, jy, e2;
 };
 
-__device__ __forceinline__ void ring_moments(const double g[8], double vk, double vk2, Mom& m) {
-  const double S = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]));
+__device__ __forceinline__ void ring_sums(const double g[8], double& S, double& X, double& Y) {
+  S = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]));
   const double a = g[0] - g[4];
   const double b = g[6] - g[2];
-  const double X = fma(kS, a + b, g[7] - g[3]);
-  const double Y = fma(kS, a - b, g[1] - g[5]);
-  m.n += S;
-  m.jx = fma(vk, X, m.jx);
-  m.jy = fma(vk, Y, m.jy);
-  m.e2 = fma(vk2, S, m.e2);
+  X = fma(kS, a + b, g[7] - g[3]);
+  Y = fma(kS, a - b, g[1] - g[5]);
+}
+
+__device__ __forceinline__ double pair_dot(double va, double xa, double vb, double xb) { return fma(va, xa, vb * xb); }
+
+__device__ __forceinline__ Mom combine_rings(double f0, const double S[4], const double X[4], const double Y[4],
+                                             const Coeffs& c) {
+  Mom m;
+  m.n = ((f0 + S[0]) + S[1]) + (S[2] + S[3]);
+  m.jx = pair_dot(c.v[0], X[0], c.v[1], X[1]) + pair_dot(c.v[2], X[2], c.v[3], X[3]);
+  m.jy = pair_dot(c.v[0], Y[0], c.v[1], Y[1]) + pair_dot(c.v[2], Y[2], c.v[3], Y[3]);
+  m.e2 = pair_dot(c.v2[0], S[0], c.v2[1], S[1]) + pair_dot(c.v2[2], S[2], c.v2[3], S[3]);
+  return m;
 }
 
 __device__ __forceinline__ Mom node_moments(const double* __restrict__ f, long long plane, long long off,
                                             const Coeffs& c) {
-  Mom m;
-  m.n = ld(f + off);
-  m.jx = 0.0;
-  m.jy = 0.0;
-  m.e2 = 0.0;
+  double S[4], X[4], Y[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     double g[8];
 #pragma unroll
     for (int d = 0; d < 8; ++d) g[d] = ld(f + (long long)(1 + 8 * k + d) * plane + off);
-    ring_moments(g, c.v[k], c.v2[k], m);
+    ring_sums(g, S[k], X[k], Y[k]);
   }
-  return m;
+  return combine_rings(ld(f + off), S, X, Y, c);
 }
 
-// FP32 storage: the 33 values are widened to FP64 exactly (integer path), then summed in FP64.
+// FP32 storage: the 33 values are widened to FP64 exactly, then summed in FP64. The integer path
+// serves normal numbers; a node holding a zero, subnormal or non-finite value takes the hardware
+// conversion (a separate branch, so the common path issues no FP64 conversions).
+__device__ __forceinline__ Mom moments_from(const float (&x)[Q], const Coeffs& c, bool hw) {
+  double S[4], X[4], Y[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double g[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) g[d] = hw ? (double)x[1 + 8 * k + d] : f32_to_f64_bits(x[1 + 8 * k + d]);
+    ring_sums(g, S[k], X[k], Y[k]);
+  }
+  return combine_rings(hw ? (double)x[0] : f32_to_f64_bits(x[0]), S, X, Y, c);
+}
+
 __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long long plane, long long off,
                                             const Coeffs& c) {
   float x[Q];
@@ -251,30 +273,40 @@ __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long lo
     x[q] = ld(f + (long long)q * plane + off);
     special |= f32_special(x[q]);
   }
-  Mom m;
-  m.jx = 0.0;
-  m.jy = 0.0;
-  m.e2 = 0.0;
-  if (!special) {
-    m.n = f32_to_f64_bits(x[0]);
+  if (!special) return moments_from(x, c, false);
+  return moments_from(x, c, true);
+}
+
+// One ring of a node (ring-parallel kernel): S, X, Y of ring k, and f_0 (read by every lane).
+__device__ __forceinline__ void ring_of_node(const double* __restrict__ f, long long plane, long long off, int k,
+                                             double& f0, double& S, double& X, double& Y) {
+  double g[8];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      double g[8];
+  for (int d = 0; d < 8; ++d) g[d] = ld(f + (long long)(1 + 8 * k + d) * plane + off);
+  f0 = ld(f + off);
+  ring_sums(g, S, X, Y);
+}
+__device__ __forceinline__ void ring_of_node(const float* __restrict__ f, long long plane, long long off, int k,
+                                             double& f0, double& S, double& X, double& Y) {
+  float x[8];
+  const float x0 = ld(f + off);
+  bool special = f32_special(x0);
 #pragma unroll
-      for (int d = 0; d < 8; ++d) g[d] = f32_to_f64_bits(x[1 + 8 * k + d]);
-      ring_moments(g, c.v[k], c.v2[k], m);
-    }
-  } else {
-    m.n = (double)x[0];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      double g[8];
-#pragma unroll
-      for (int d = 0; d < 8; ++d) g[d] = (double)x[1 + 8 * k + d];
-      ring_moments(g, c.v[k], c.v2[k], m);
-    }
+  for (int d = 0; d < 8; ++d) {
+    x[d] = ld(f + (long long)(1 + 8 * k + d) * plane + off);
+    special |= f32_special(x[d]);
   }
-  return m;
+  double g[8];
+  if (!special) {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) g[d] = f32_to_f64_bits(x[d]);
+    f0 = f32_to_f64_bits(x0);
+  } else {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) g[d] = (double)x[d];
+    f0 = (double)x0;
+  }
+  ring_sums(g, S, X, Y);
 }
 
 // (n, ux, uy, T, P) from the sums; T = (sum |v|^2 f)/(2n) - |u|^2/2  (Eq. 5 with P = nT).
@@ -340,7 +372,9 @@ struct EqRing {
 };
 __device__ __forceinline__ EqRing eq_ring(const EqSite& e, int k, const Coeffs& c) {
   EqRing r;
-  const double nF = e.rn * e.F[k];
+  // select, not e.F[k]: k may be a run-time ring index (ring-parallel kernel)
+  const double Fk = k == 0 ? e.F[0] : k == 1 ? e.F[1] : k == 2 ? e.F[2] : e.F[3];
+  const double nF = e.rn * Fk;
   r.al = nF * e.A0;
   r.be = nF * (e.A2 * c.v2[k]);
   r.ga = nF * c.v4_24[k];
@@ -445,8 +479,8 @@ struct StencilConsts<float> {
 };
 
 // Update of all 33 velocities at one interior node, given its moments and nu_x, nu_y.
-template <typename S, int K>
-__device__ __forceinline__ void update_ring(const S* __restrict__ f, S* __restrict__ fn, const Grid& g,
+template <typename S>
+__device__ __forceinline__ void update_ring(int K, const S* __restrict__ f, S* __restrict__ fn, const Grid& g,
                                             const Coeffs& c, long long off, int gx, int gy, const GhostOwn& go,
                                             const EqSite& e, S w0base, S nux, S nuy) {
   using SC = StencilConsts<S>;
@@ -486,7 +520,7 @@ __device__ __forceinline__ void update_ring(const S* __restrict__ f, S* __restri
   eq_pair_s<S>(er, e.p[3], e.x[3], fp, fm);
   out[2] = stencil_dir<S, 2>(fq + (long long)(1 + 8 * K + 2) * g.plane, g.pitch, w, fp);
   out[6] = stencil_dir<S, 6>(fq + (long long)(1 + 8 * K + 6) * g.plane, g.pitch, w, fm);
-  store_ring<S, K>(fn, g, gx, gy, go, out);
+  store_ring<S>(fn, g, gx, gy, go, K, out);
 }
 
 template <typename S>
@@ -514,21 +548,30 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
   unsigned bits = 0;
 
   // Phase 1: moments on the tile and its ring (needed: interior nodes and the ghost layer next
-  // to an edge, never the corners).
-  for (int idx = tid; idx < SW * SH; idx += NT) {
+  // to an edge, never the corners). Branch-free and unrolled over a thread's slots, so the FP64
+  // chains of its 2-3 nodes interleave: every slot loads from an address clamped into the padded
+  // grid, and only needed nodes are stored and health-checked.
+  constexpr int NSLOT = (SW * SH + NT - 1) / NT;
+#pragma unroll
+  for (int k = 0; k < NSLOT; ++k) {
+    const int idx = tid + k * NT;
+    // the slots before the last always lie in the tile ring (no branch); the last one is guarded
+    if ((k + 1) * NT > SW * SH && idx >= SW * SH) continue;
     const int lx = idx % SW, ly = idx / SW;
     const int gx = x0 + lx - 1, gy = y0 + ly - 1;
     const bool inx = gx >= 0 && gx < g.nx, iny = gy >= 0 && gy < g.ny;
     const bool need = (inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny));
-    if (!need) continue;
-    const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
+    const int cx = min(max(gx, -1), g.nx), cy = min(max(gy, -1), g.ny);  // inside the padded grid
+    const long long off = (long long)(cy + NG) * g.pitch + (cx + NG);
     const Macro m = to_macro(node_moments(f, g.plane, off, c));
-    if (!macro_ok(m)) bits |= H_NUMERIC;
-    s_n[ly][lx] = m.n;
-    s_ux[ly][lx] = m.ux;
-    s_uy[ly][lx] = m.uy;
-    s_T[ly][lx] = m.T;
-    s_P[ly][lx] = from_d<S>(m.P);
+    if (need) {
+      if (!macro_ok(m)) bits |= H_NUMERIC;
+      s_n[ly][lx] = m.n;
+      s_ux[ly][lx] = m.ux;
+      s_uy[ly][lx] = m.uy;
+      s_T[ly][lx] = m.T;
+      s_P[ly][lx] = from_d<S>(m.P);
+    }
   }
   __syncthreads();
 
@@ -570,10 +613,10 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       acc = fma(snuy, ld(p + g.pitch) + ld(p - g.pitch), acc);
       store_node<S, 0>(fn, g, gx, gy, go, acc);
     }
-    update_ring<S, 0>(f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
-    update_ring<S, 1>(f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
-    update_ring<S, 2>(f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
-    update_ring<S, 3>(f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S>(0, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S>(1, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S>(2, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S>(3, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
   }
   if (bits) atomicOr(health, bits);
 }
@@ -610,6 +653,114 @@ __global__ void __launch_bounds__(BX * BY, MINB) k_step_batch(const BatchMember*
   const S* in = static_cast<const S*>(m.f[par]);
   S* out = static_cast<S*>(m.f[par ^ 1]);
   step_tile<S, BX, BY, RY>(in, out, g, c, m.health, tx, ty);
+}
+
+// Ring-parallel step for small grids, where one thread per node leaves the GPU's FP64 pipes
+// waiting on long dependency chains. Four lanes share a node, lane r holding velocity ring r:
+// - Moments: each lane sums its ring. Two shuffle stages combine the rings in the same pairwise
+//   tree as node_moments, so the sums are bit for bit those of k_step.
+// - Update: all four lanes evaluate the node's constants (switch, weights, f_eq site terms).
+//   That costs no extra issue slots: it is one warp instruction whether one lane or four use it.
+//   Each lane then updates its own 8 velocities, and lane 0 also the rest velocity.
+// Each thread thus issues about half of k_step's FP64 chain. Results are bitwise those of k_step.
+template <typename S, int TW, int TH>
+__global__ void __launch_bounds__(4 * TW * TH) k_step_rp(const S* __restrict__ f, S* __restrict__ fn, Grid g,
+                                                       Coeffs c, unsigned* __restrict__ health) {
+  constexpr int SW = TW + 2, SH = TH + 2, NQ = TW * TH;
+  using SC = StencilConsts<S>;
+  __shared__ double s_n[SH][SW], s_ux[SH][SW], s_uy[SH][SW], s_T[SH][SW];
+  __shared__ S s_P[SH][SW];
+  const int r = threadIdx.x & 3, quad = threadIdx.x >> 2;
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+  const unsigned FULL = 0xffffffffu;
+  unsigned bits = 0;
+
+  // Phase 1: moments on the tile and its ring; every lane takes part in every shuffle.
+  constexpr int NSLOT = (SW * SH + NQ - 1) / NQ;
+#pragma unroll
+  for (int k = 0; k < NSLOT; ++k) {
+    const int idx = quad + k * NQ;
+    const bool inslot = idx < SW * SH;
+    const int lx = inslot ? idx % SW : 0, ly = inslot ? idx / SW : 0;
+    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    const bool inx = gx >= 0 && gx < g.nx, iny = gy >= 0 && gy < g.ny;
+    const bool need =
+        inslot && ((inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny)));
+    const int cx = min(max(gx, -1), g.nx), cy = min(max(gy, -1), g.ny);
+    const long long off = (long long)(cy + NG) * g.pitch + (cx + NG);
+    double f0, Sr, Xr, Yr;
+    ring_of_node(f, g.plane, off, r, f0, Sr, Xr, Yr);
+    // stage 1 (lanes r, r^1): n pair = (f0 + S_0) + S_1 or S_2 + S_3; j pair = fma(v_e, X_e, v_o X_o)
+    const bool even = (r & 1) == 0;
+    const double pn = (r == 0) ? f0 + Sr : Sr;
+    const double prodx = c.v[r] * Xr, prody = c.v[r] * Yr, prode = c.v2[r] * Sr;
+    // the even lane sends its X (Y, S), the odd lane its product v X; each then forms
+    // fma(v_even, X_even, v_odd X_odd) from identical operands
+    const double o_pn = __shfl_xor_sync(FULL, pn, 1);
+    const double o_x = __shfl_xor_sync(FULL, even ? Xr : prodx, 1);
+    const double o_y = __shfl_xor_sync(FULL, even ? Yr : prody, 1);
+    const double o_e = __shfl_xor_sync(FULL, even ? Sr : prode, 1);
+    const int re = r & 2;  // the even lane of the pair
+    double n2 = pn + o_pn;
+    double jx2 = even ? fma(c.v[re], Xr, o_x) : fma(c.v[re], o_x, prodx);
+    double jy2 = even ? fma(c.v[re], Yr, o_y) : fma(c.v[re], o_y, prody);
+    double e22 = even ? fma(c.v2[re], Sr, o_e) : fma(c.v2[re], o_e, prode);
+    // stage 2 (pairs 01 and 23): commutative sums, equal in all four lanes
+    Mom m;
+    m.n = n2 + __shfl_xor_sync(FULL, n2, 2);
+    m.jx = jx2 + __shfl_xor_sync(FULL, jx2, 2);
+    m.jy = jy2 + __shfl_xor_sync(FULL, jy2, 2);
+    m.e2 = e22 + __shfl_xor_sync(FULL, e22, 2);
+    const Macro mm = to_macro(m);
+    if (need && r == 0) {
+      if (!macro_ok(mm)) bits |= H_NUMERIC;
+      s_n[ly][lx] = mm.n;
+      s_ux[ly][lx] = mm.ux;
+      s_uy[ly][lx] = mm.uy;
+      s_T[ly][lx] = mm.T;
+      s_P[ly][lx] = from_d<S>(mm.P);
+    }
+  }
+  __syncthreads();
+
+  // Phase 2: the quad's node.
+  const int tx = quad % TW, ty = quad / TW;
+  const int gx = x0 + tx, gy = y0 + ty;
+  if (gx < g.nx && gy < g.ny) {
+    const int lx = tx + 1, ly = ty + 1;
+    const double n = s_n[ly][lx], ux = s_ux[ly][lx], uy = s_uy[ly][lx], T = s_T[ly][lx];
+    S thx, thy;
+    if (g.flags & F_SWITCH_CONST) {
+      thx = SC::lam(c);
+      thy = SC::lam(c);
+    } else {
+      const S P0 = s_P[ly][lx];
+      const S sx = s_P[ly][lx + 1] + s_P[ly][lx - 1], sy = s_P[ly + 1][lx] + s_P[ly - 1][lx];
+      thx = SC::lam(c) * fabs(fma((S)-2, P0, sx) * recip(fma((S)2, P0, sx)));
+      thy = SC::lam(c) * fabs(fma((S)-2, P0, sy) * recip(fma((S)2, P0, sy)));
+    }
+    const S akx = fabs(from_d<S>(ux) * SC::kx(c)), aky = fabs(from_d<S>(uy) * SC::ky(c));
+    if (r == 0 && (akx > (S)1 || aky > (S)1)) bits |= H_KAPPA;
+    S snux = 0, snuy = 0;
+    if (!(g.flags & F_NO_VISC)) {
+      snux = (S)0.5 * thx * akx * ((S)1 - akx);
+      snuy = (S)0.5 * thy * aky * ((S)1 - aky);
+    }
+    const S w0base = ((S)1 - SC::r(c)) - (S)2 * (snux + snuy);
+    const EqSite e = eq_site(n, ux, uy, T, c);
+    const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
+    const GhostOwn go = ghost_own(g, gx, gy);
+    if (r == 0) {
+      const S rfeq = to_s<S>(e.rn * e.F0 * e.A0);
+      const S* p = f + off;
+      S acc = fma(w0base, ld(p), rfeq);
+      acc = fma(snux, ld(p + 1) + ld(p - 1), acc);
+      acc = fma(snuy, ld(p + g.pitch) + ld(p - g.pitch), acc);
+      store_node<S, 0>(fn, g, gx, gy, go, acc);
+    }
+    update_ring<S>(r, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+  }
+  if (bits) atomicOr(health, bits);
 }
 
 // health words of the members into one array (one device-to-host copy per batch round)
@@ -766,10 +917,19 @@ cudaError_t launch_batch_v(int variant, const BatchMember* mem, int nmem, long l
   }
 }
 
+template <typename S, int TW, int TH>
+cudaError_t launch_rp_t(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health, cudaStream_t s) {
+  dim3 grid((g.nx + TW - 1) / TW, (g.ny + TH - 1) / TH);
+  k_step_rp<S, TW, TH><<<grid, 4 * TW * TH, 0, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g, c, health);
+  return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_step_v(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
   switch (variant) {
+    case V_RP16x4: return launch_rp_t<S, 16, 4>(f, fn, g, c, health, s);
+    case V_RP8x4: return launch_rp_t<S, 8, 4>(f, fn, g, c, health, s);
     case V_T32x4: return launch_step_t<S, 32, 4, 1, 4>(f, fn, g, c, health, s);
     case V_T32x8: return launch_step_t<S, 32, 4, 2, 4>(f, fn, g, c, health, s);
     case V_T32x16: return launch_step_t<S, 32, 8, 2, 2>(f, fn, g, c, health, s);

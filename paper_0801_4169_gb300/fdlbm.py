@@ -36,6 +36,23 @@ class fdlbm_config(ctypes.Structure):
                 ("bc", ctypes.c_int * 4), ("prec", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
+class fdlbm_request(ctypes.Structure):
+    _fields_ = [("cfg", fdlbm_config), ("bstate", (ctypes.c_double * 4) * 4),
+                ("rho", ctypes.POINTER(ctypes.c_double)), ("u", ctypes.POINTER(ctypes.c_double)),
+                ("v", ctypes.POINTER(ctypes.c_double)), ("T", ctypes.POINTER(ctypes.c_double)),
+                ("steps", ctypes.c_long), ("sim_fail_step", ctypes.c_long)]
+
+
+class fdlbm_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("done", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("queued", ctypes.c_longlong), ("rounds", ctypes.c_longlong), ("max_active", ctypes.c_int),
+                ("max_bytes", ctypes.c_size_t), ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double),
+                ("mean_s", ctypes.c_double), ("wall_s", ctypes.c_double), ("aggregate_glups", ctypes.c_double)]
+
+
+FDLBM_REQ_QUEUED, FDLBM_REQ_ACTIVE, FDLBM_REQ_DONE, FDLBM_REQ_FAILED, FDLBM_REQ_CANCELLED = 0, 1, 2, 3, 4
+FDLBM_ENGINE_GPU, FDLBM_ENGINE_SIMULATED, FDLBM_ENGINE_GPU_SEPARATE = 0, 1, 2
+
 _lib = None
 _DP = ctypes.POINTER(ctypes.c_double)
 _VP = ctypes.c_void_p
@@ -93,6 +110,16 @@ def lib():
             "fdlbm_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
             "fdlbm_batch_destroy": (ctypes.c_int, [_VP]),
             "fdlbm_batch_last_error": (ctypes.c_char_p, [_VP]),
+            "fdlbm_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_size_t, ctypes.c_int, ctypes.c_long,
+                                                   ctypes.c_int, _VP]),
+            "fdlbm_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(fdlbm_request),
+                                                   ctypes.POINTER(ctypes.c_longlong)]),
+            "fdlbm_server_poll": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
+            "fdlbm_server_wait": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+            "fdlbm_server_result": (ctypes.c_int, [_VP, ctypes.c_longlong, _DP, _DP, _DP, _DP, _DP]),
+            "fdlbm_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(fdlbm_server_stats_t)]),
+            "fdlbm_server_destroy": (ctypes.c_int, [_VP]),
+            "fdlbm_server_last_error": (ctypes.c_char_p, [_VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -315,6 +342,75 @@ def fdlbm_batch_destroy(b):
 
 def fdlbm_batch_last_error(b):
     s = lib().fdlbm_batch_last_error(b)
+    return s.decode() if s else ""
+
+
+def _scheck(srv, rc):
+    if rc < 0:
+        raise FdlbmError(rc, fdlbm_server_last_error(srv))
+    return rc
+
+
+def fdlbm_server_create(budget_bytes, max_slots=256, round_steps=500, engine=FDLBM_ENGINE_GPU, stream=None):
+    srv = _VP()
+    _scheck(None, lib().fdlbm_server_create(ctypes.byref(srv), int(budget_bytes), int(max_slots), int(round_steps),
+                                            int(engine), _stream_ptr(stream)))
+    return srv.value
+
+
+def fdlbm_server_submit(srv, cfg, rho, u, v, T, steps, bstate=None, sim_fail_step=0):
+    n = cfg.nx * cfg.ny
+    arrs = [_host(a, n) for a in (rho, u, v, T)]
+    req = fdlbm_request()
+    req.cfg = cfg
+    if bstate is not None:
+        for i in range(4):
+            for j in range(4):
+                req.bstate[i][j] = float(bstate[i][j])
+    req.rho, req.u, req.v, req.T = [_hp(a) for a in arrs]
+    req.steps = int(steps)
+    req.sim_fail_step = int(sim_fail_step)
+    rid = ctypes.c_longlong()
+    _scheck(srv, lib().fdlbm_server_submit(srv, ctypes.byref(req), ctypes.byref(rid)))
+    return rid.value
+
+
+def fdlbm_server_poll(srv, rid):
+    st = ctypes.c_int()
+    _scheck(srv, lib().fdlbm_server_poll(srv, int(rid), ctypes.byref(st)))
+    return st.value
+
+
+def fdlbm_server_wait(srv, rid, timeout_s=-1.0):
+    """Returns the final status, or None if the timeout ran out first."""
+    st = ctypes.c_int()
+    rc = lib().fdlbm_server_wait(srv, int(rid), float(timeout_s), ctypes.byref(st))
+    if rc == FDLBM_E_TIMEOUT:
+        return None
+    _scheck(srv, rc)
+    return st.value
+
+
+def fdlbm_server_result(srv, rid, nx, ny):
+    """(rho, u, v, T, seconds_to_solution) of a finished request; raises FdlbmError for a failed one."""
+    out = [np.empty((ny, nx)) for _ in range(4)]
+    secs = ctypes.c_double()
+    _scheck(srv, lib().fdlbm_server_result(srv, int(rid), *[_hp(a) for a in out], ctypes.byref(secs)))
+    return tuple(out) + (secs.value,)
+
+
+def fdlbm_server_stats(srv):
+    st = fdlbm_server_stats_t()
+    _scheck(srv, lib().fdlbm_server_stats(srv, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+def fdlbm_server_destroy(srv):
+    return lib().fdlbm_server_destroy(srv)
+
+
+def fdlbm_server_last_error(srv):
+    s = lib().fdlbm_server_last_error(srv)
     return s.decode() if s else ""
 
 

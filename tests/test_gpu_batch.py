@@ -145,7 +145,8 @@ def test_batch_autotune_keeps_state():
     F.fdlbm_batch_sync(b)
     before = [s.get_f() for s in ss]
     times = F.fdlbm_batch_autotune(b, 2)
-    assert len(times) == F.fdlbm_variant_count() and all(t > 0 for t in times)
+    # the tile variants (0-7) are timed; the ring-parallel ones are single-solve only (reported 0)
+    assert len(times) == F.fdlbm_variant_count() and all(t > 0 for t in times[:8])
     F.fdlbm_batch_sync(b)
     for s, f in zip(ss, before):
         assert np.array_equal(s.get_f(), f) and s.steps_done == 3
@@ -159,25 +160,27 @@ def test_batch_autotune_keeps_state():
 
 
 def test_serving_results_equal_alone_runs():
-    """Continuous batching: 20 requests arriving over time; every finished request's moments
-    equal those of the same solve run alone; the separate-launch baseline agrees too."""
-    reqs = W.serving_requests(n=20, seed=11, nx_range=(256, 2048), steps_range=(50, 400))
-    results = {}
-    for mode in ("batched", "separate"):
-        eng = serve.GpuEngine(mode=mode)
-        sch = serve.Scheduler(eng, budget_bytes=64 << 20, round_steps=37)
-        out = sch.run([W.Request(**vars(r)) for r in reqs], realtime=False)
-        assert out["requests_done"] + out["failed"] == len(reqs)
-        results[mode] = {j.req.rid: j for j in sch.finished}
-    for rid, j in results["batched"].items():
-        js = results["separate"][rid]
-        assert j.status == js.status
-        if j.status != "done":
-            assert j.req.prec == F.FDLBM_FP32_STORE  # only FP32 storage fails on these states
+    """Continuous batching in the native runtime: 24 requests arriving over time, mixed sizes, Mach
+    numbers and precisions. Every finished request's moments equal those of the same solve run
+    alone, for the batched engine and for the separate-launch baseline alike, and the two engines
+    fail the same requests (FP32 storage on ill-conditioned states)."""
+    reqs = W.serving_requests(n=24, seed=11, nx_range=(256, 2048), steps_range=(50, 400), mean_gap_s=0.002)
+    outcomes = {}
+    for engine in ("gpu", "separate"):
+        srv = serve.Server(budget_bytes=64 << 20, round_steps=37, engine=engine)
+        out, st = serve.replay(srv, [W.Request(**vars(r)) for r in reqs])
+        srv.close()
+        assert st["done"] + st["failed"] == len(reqs) and st["max_bytes"] <= 64 << 20
+        outcomes[engine] = {r.rid: (status, macros) for (r, status, macros, secs, err) in out.values()}
+    for r in reqs:
+        sb, mb = outcomes["gpu"][r.rid]
+        ss, ms = outcomes["separate"][r.rid]
+        assert sb == ss
+        if sb != F.FDLBM_REQ_DONE:
+            assert r.prec == F.FDLBM_FP32_STORE  # only FP32 storage fails on these states
             continue
-        w = W.request_workload(j.req)
-        a = F.Solver.from_workload(w, j.req.prec)
-        a.step(j.req.steps)
+        a = F.Solver.from_workload(W.request_workload(r), r.prec)
+        a.step(r.steps)
         ref = a.get_macro(check=False)
-        for got, got_sep, r in zip(j.result, js.result, ref):
-            assert np.array_equal(got, r) and np.array_equal(got_sep, r)
+        for got_b, got_s, want in zip(mb, ms, ref):
+            assert np.array_equal(got_b, want) and np.array_equal(got_s, want)
