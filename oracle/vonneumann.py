@@ -22,7 +22,23 @@ Reading: the switch theta_alphaI of Eq. 16 is quadratic in a perturbation
 and drops out of a linearisation, yet Sec. 4 varies lambda, so the analysis
 holds theta_alphaI at lambda (the oracle's SWITCH_CONST flag is the matching
 simulation).
+
+High precision (``*_mp``). At the high-Mach states of Sec. 4 the eigenvalues of
+G are extremely sensitive: at (rho, u1, u2, T) = (2, 30, 0, 1) a relative
+perturbation of G of 1e-16 moves them by O(1), while 1e-32 moves them by
+1e-16. The entries of G carry the cancellation of the 4th-order f^eq at
+s = v.u/theta ~ 135. So FP64 eigenvalues there mean nothing. The ``*_mp``
+functions build G from Eqs. 10-13 and 18-20 in mpmath at ``dps`` decimal digits:
+- f^eq is restated from Eq. 10;
+- its T and u derivatives are taken by mpmath's numerical differentiation at
+  that precision;
+- the eigenvalues come from mpmath's QR.
+The speeds are the binary64 values nearest 1, 1.92, 2.99, 4.49, converted
+exactly, so the model is the one the C oracle and the CUDA library use. The
+direction cosines are exact. The results hold to about dps - 20 digits at the
+worst states of Sec. 4.
 """
+import mpmath as mp
 import numpy as np
 
 from . import fdlbm as _o
@@ -98,3 +114,107 @@ def max_growth(state, dx, dy, dt, tau, lam=0.0, nk=64, axis="x", **kw):
         kx, ky = (xi, 0.0) if axis == "x" else (0.0, xi)
         best = max(best, max_abs_eig(amplification_matrix(state, kx, ky, dx, dy, dt, tau, lam, J=J, **kw)))
     return best
+
+
+# ---------------------------------------------------------------------------------------------
+# high precision (mpmath)
+
+def _mp_velocities():
+    """Eq. 1 with exact direction cosines: q = 1 + 8(k-1) + (i-1), direction i at angle i pi/4."""
+    speeds = [mp.mpf(1.0), mp.mpf(1.92), mp.mpf(2.99), mp.mpf(4.49)]  # binary64 values, exactly
+    vx, vy = [mp.mpf(0)], [mp.mpf(0)]
+    for k in range(4):
+        for i in range(1, 9):
+            vx.append(speeds[k] * mp.cos(i * mp.pi / 4))
+            vy.append(speeds[k] * mp.sin(i * mp.pi / 4))
+    # cos/sin of multiples of pi/4 are 0, +-1 or +-sqrt(1/2): snap the zeros and ones exactly
+    for v in (vx, vy):
+        for q in range(1, Q):
+            sp = speeds[(q - 1) // 8]
+            r = v[q] / sp
+            if abs(r) < mp.mpf(10) ** (-mp.mp.dps + 5):
+                v[q] = mp.mpf(0)
+            elif abs(abs(r) - 1) < mp.mpf(10) ** (-mp.mp.dps + 5):
+                v[q] = sp * mp.sign(r)
+    return speeds, vx, vy
+
+
+def _mp_weights(speeds, theta):
+    """(F_0, F_1..F_4) of Eqs. 11-13 with the cyclic index {k+l}."""
+    F = []
+    for k in range(4):
+        vk2 = speeds[k] ** 2
+        a, b, c = (speeds[(k + l) % 4] ** 2 for l in (1, 2, 3))
+        denom = vk2 * (vk2 - a) * (vk2 - b) * (vk2 - c)
+        F.append((48 * theta ** 4 - 6 * (a + b + c) * theta ** 3 + (a * b + b * c + c * a) * theta ** 2
+                  - a * b * c / 4 * theta) / denom)
+    return [1 - 8 * sum(F)] + F
+
+
+def feq_mp(n, ux, uy, T, dps=50):
+    """f^eq (33 mpf) of Eq. 10, all five terms inside n F_k [...], theta = T (m = 1)."""
+    with mp.workdps(dps):
+        speeds, vx, vy = _mp_velocities()
+        return _feq_mp(speeds, vx, vy, mp.mpf(n), mp.mpf(ux), mp.mpf(uy), mp.mpf(T))
+
+
+def _feq_mp(speeds, vx, vy, n, ux, uy, T):
+    F = _mp_weights(speeds, T)
+    u2 = ux * ux + uy * uy
+    out = []
+    for q in range(Q):
+        Fk = F[0] if q == 0 else F[1 + (q - 1) // 8]
+        vu = vx[q] * ux + vy[q] * uy
+        br = (1 - u2 / (2 * T) + u2 * u2 / (8 * T * T)
+              + (vu / T) * (1 - u2 / (2 * T))
+              + vu * vu / (2 * T * T) * (1 - u2 / (2 * T))
+              + vu ** 3 / (6 * T ** 3) + vu ** 4 / (24 * T ** 4))
+        out.append(n * Fk * br)
+    return out
+
+
+def amplification_matrix_mp(state, kx_dx, ky_dy, dx, dy, dt, tau, lam=0.0,
+                            lw=True, disp=True, visc=True, dps=50):
+    """G of Eq. 18 (mpmath matrix at dps digits); same terms and switches as amplification_matrix."""
+    with mp.workdps(dps):
+        speeds, vx, vy = _mp_velocities()
+        n, ux, uy, T = (mp.mpf(x) for x in state)
+        fe = _feq_mp(speeds, vx, vy, n, ux, uy, T)
+        dT = [mp.diff(lambda t, q=q: _feq_mp(speeds, vx, vy, n, ux, uy, t)[q], T) for q in range(Q)]
+        dux = [mp.diff(lambda a, q=q: _feq_mp(speeds, vx, vy, n, a, uy, T)[q], ux) for q in range(Q)]
+        duy = [mp.diff(lambda a, q=q: _feq_mp(speeds, vx, vy, n, ux, a, T)[q], uy) for q in range(Q)]
+        r = mp.mpf(dt) / mp.mpf(tau)
+        G = mp.matrix(Q, Q)
+        for j in range(Q):
+            wx, wy = vx[j] - ux, vy[j] - uy
+            cT = ((wx * wx + wy * wy) / 2 - T) / n
+            for i in range(Q):  # Eq. 20
+                G[i, j] = r * (fe[i] / n + dT[i] * cT + dux[i] * wx / n + duy[i] * wy / n)
+        for i in range(Q):
+            G[i, i] += 1 - r
+            for xi, va, dr, ua in ((mp.mpf(kx_dx), vx, mp.mpf(dx), ux), (mp.mpf(ky_dy), vy, mp.mpf(dy), uy)):
+                c = va[i] * mp.mpf(dt) / dr
+                e1, e2 = mp.expj(xi), mp.expj(2 * xi)
+                d = -(c / 2) * (e1 - 1 / e1)
+                if lw:
+                    d += (c * c / 2) * (e1 - 2 + 1 / e1)
+                if disp:
+                    d += c * (1 - c * c) / 12 * (e2 - 2 * e1 + 2 / e1 - 1 / e2)
+                if visc:
+                    kap = abs(ua * mp.mpf(dt) / dr)
+                    d += mp.mpf(lam) * kap * (1 - kap) / 2 * (e1 - 2 + 1 / e1)
+                G[i, i] += d
+        return G
+
+
+def eigvals_mp(G, dps=50):
+    """The 33 eigenvalues of an mpmath matrix, as mpc, by mpmath's QR at dps digits."""
+    with mp.workdps(dps):
+        return list(mp.eig(G, left=False, right=False))
+
+
+def max_abs_eig_mp(state, kx_dx, ky_dy, dx, dy, dt, tau, lam=0.0, dps=50, **kw):
+    """max |omega| of G (Eq. 18) at dps digits, returned as a float."""
+    G = amplification_matrix_mp(state, kx_dx, ky_dy, dx, dy, dt, tau, lam, dps=dps, **kw)
+    with mp.workdps(dps):
+        return float(max(abs(z) for z in eigvals_mp(G, dps)))
