@@ -20,6 +20,12 @@ above the 129 MB L2, so no L2 flush is needed between steps.
 
 N > 1 (torchrun): every rank runs an independent replica with its own seed (weak scaling, no
 data-path collective); the time is the max over ranks.
+
+--workload vn_sec4 benchmarks the von Neumann tool instead (Sec. 4, Eqs. 18-20): a "step" is one
+fdlbm_vn_spectrum call over every curve of Figs. 2, 4, 5 and 6 at 256 wave numbers (5632 33 x 33
+complex eigenproblems in double-double). The metric is amplification-matrix spectra per second.
+Its oracle is the 40-digit mpmath computation in oracle/vonneumann.py, because FP64 eigenvalues
+are wrong at these states.
 """
 import argparse
 import json
@@ -39,6 +45,10 @@ sys.path.insert(0, ROOT)
 FP64_OPS_PER_LUP = {"fp64": 579, "fp32": 228}
 # Minimum HBM bytes per site update: read and write all 33 f once.
 BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4}
+# FP64 instructions (DADD + DFMA + DMUL) per amplification-matrix spectrum of the von Neumann
+# tool on the Sec. 4 sweep: ncu thread-level counts of k_vn divided by the cases. They include the
+# rotation parameters every lane computes alike, so they bound the algorithmic work from above.
+FP64_OPS_PER_VN_MATRIX = 16.46e6
 # FP64 issue peak: 2 instructions per clock per SM, i.e. the nominal 1.25 TFLOP/s at 2.07 GHz
 # (ncu's pct-of-peak for the FP64 pipe agrees with it).
 FP64_OPS_PER_CLK_SM = 2.0
@@ -160,9 +170,41 @@ def oracle_sample(name, budget_s=20.0):
             "sample": "%s, %d steps, %.1f s single-threaded FP64 C" % (sample, steps, el)}
 
 
+def vn_oracle_sample(budget_s=20.0):
+    """The 40-digit oracle (mpmath) on the first cases of the Sec. 4 sweep, spread over its curves."""
+    from oracle import vonneumann as V
+    from paper_0801_4169_gb300 import workloads as W
+    rows, curves, xi = W.vn_sec4_cases(nk=256)
+    dx, dy, dt, tau = W.VN_SEC4_GRID
+    order = np.arange(len(rows)).reshape(len(curves), len(xi)).T.ravel()  # one per curve, then the next k
+    done = 0
+    t0 = time.perf_counter()
+    for i in order:
+        r = rows[i]
+        fl = int(r[7])
+        V.max_abs_eig_mp(tuple(r[:4]), r[4], r[5], dx, dy, dt, tau, r[6], dps=40, lw=not fl & 1, disp=not fl & 2,
+                         visc=not fl & 4)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "matrices/s", "cores": 1, "kind": "oracle",
+            "sample": "%d of the %d Sec. 4 cases at 40 digits (mpmath), %.1f s single-threaded" % (done, len(rows), el)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "vn_sec4":
+        cb = vn_oracle_sample(budget_s=max(5.0, min(60.0, 4.0 * args.steps)))
+        line = {"impl": "reference", "metric": "amplification-matrix spectra/s", "value": cb["value"],
+                "unit": "matrices/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mp40",
+                "data": "synthetic", "config": {"workload": "vn_sec4", "impl": "40-digit oracle (oracle/vonneumann.py)"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     cb = oracle_sample(args.workload, budget_s=max(5.0, min(60.0, 4.0 * args.steps)))
     line = {"impl": "reference", "metric": "GLUPS", "value": cb["value"], "unit": "GLUPS", "n_gpus": args.gpus,
@@ -174,13 +216,92 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_vn(args, F, torch, dist, rank, local, world):
+    """The von Neumann tool on the Sec. 4 sweep (see the module docstring)."""
+    from paper_0801_4169_gb300 import workloads as W
+    rows, curves, xi = W.vn_sec4_cases(nk=256)
+    dx, dy, dt, tau = W.VN_SEC4_GRID
+    cases = F.vn_cases(rows[:, :4], rows[:, 4], rows[:, 5], rows[:, 6], rows[:, 7].astype(np.int32))
+    n = len(cases)
+    stream = torch.cuda.Stream()
+    raw = cases.view(np.uint8)
+    h_cases = torch.empty(raw.shape, dtype=torch.uint8, pin_memory=True)
+    h_cases.numpy()[...] = raw
+    h_max = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    with torch.cuda.stream(stream):
+        d_cases = h_cases.to("cuda", non_blocking=True)
+        d_max = torch.empty(n, dtype=torch.float64, device="cuda")
+        d_st = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        F.fdlbm_vn_spectrum(d_cases, n, dx, dy, dt, tau, d_max, None, None, d_st, stream)
+    stream.synchronize()
+    sampler = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    for _ in range(args.steps):
+        F.fdlbm_vn_spectrum(d_cases, n, dx, dy, dt, tau, d_max, None, None, d_st, stream)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    st = d_st.cpu().numpy()
+    if dist:
+        dist.barrier()
+    ms_max, work, _ = aggregate_over_ranks(ms, n * args.steps, dist, device="cuda")
+    rate = work / (ms_max * 1e-3)
+    # end to end: pinned host cases in, max |omega| out, every step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            d_cases.copy_(h_cases, non_blocking=True)
+        F.fdlbm_vn_spectrum(d_cases, n, dx, dy, dt, tau, d_max, None, None, d_st, stream)
+        with torch.cuda.stream(stream):
+            h_max.copy_(d_max, non_blocking=True)
+        stream.synchronize()
+    t_e2e = time.perf_counter() - t0
+    t_e2e_max, e2e_work, _ = aggregate_over_ranks(t_e2e * 1e3, n * args.steps, dist, device="cuda")
+    e2e_rate = e2e_work / (t_e2e_max * 1e-3)
+    peaks, peak_kind = load_peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * sm_mhz * 1e6 / 1e9
+    per_launch_rate = n / (ms / args.steps * 1e-3)
+    achieved = FP64_OPS_PER_VN_MATRIX * per_launch_rate / 1e9 if FP64_OPS_PER_VN_MATRIX else None
+    line = {
+        "metric": "amplification-matrix spectra/s", "value": rate, "unit": "matrices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64x2 (double-double)", "data": "synthetic",
+        "config": {"workload": "vn_sec4", "cases": n, "curves": len(curves), "nk": len(xi),
+                   "l2": "inputs of %d KB: every step reads the same cases (compute-bound, no flush)" % (raw.size // 1024),
+                   "status_counts": np.bincount(st, minlength=3).tolist(), "parallelism": "replicas%d" % world},
+        "roofline": {"bound": "alu", "kernel": "k_vn", "achieved": achieved, "peak": fp64_peak,
+                     "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak if achieved else None, "traffic": None,
+                     "peak_derivation": "2 FP64 ops/clk/SM (nominal 1.25 TFLOP/s) x 152 SMs x %.0f MHz sampled" % sm_mhz},
+        "clocks": clocks,
+        "e2e": {"value": e2e_rate, "unit": "matrices/s", "h2d_bytes_per_step": int(raw.size),
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = vn_oracle_sample(budget_s=20.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="riemann4096",
-                    choices=["riemann4096", "reflection1200x300", "shock4000x4", "sod400x4"])
+                    choices=["riemann4096", "reflection1200x300", "shock4000x4", "sod400x4", "vn_sec4"])
     ap.add_argument("--prec", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -202,6 +323,11 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "vn_sec4":
+        run_vn(args, F, torch, dist, rank, local, world)
+        if dist:
+            dist.destroy_process_group()
+        return
     prec_name = args.prec or ("fp64" if args.workload == "sod400x4" else "fp32")
     prec = F.FDLBM_FP64 if prec_name == "fp64" else F.FDLBM_FP32_STORE
 

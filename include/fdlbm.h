@@ -337,6 +337,57 @@ const char* fdlbm_server_last_error(fdlbm_server_t s);
 int fdlbm_step_noalloc(const fdlbm_config* cfg, void* f_a, void* f_b, long nsteps, long* first_bad_step,
                        void* cuda_stream);
 
+/* ---- von Neumann analysis (Sec. 4, Eqs. 18-20) ----------------------------------------------
+ *
+ * A small Fourier perturbation of a uniform equilibrium (rho, u1, u2, T) on a periodic grid is
+ * amplified each step by the 33 x 33 matrix
+ *   G = (1 - dt/tau) I + (dt/tau) d f^eq/d f + diag(symbol of Eq. 17, lines I-IV)   (Eq. 18),
+ * with the equilibrium Jacobian taken through rho, T and u (Eq. 20). The scheme is stable at that
+ * state when max |omega| <= 1 over the wave numbers. Readings: the switch theta_alphaI of Eq. 16,
+ * quadratic in the perturbation, is held at lambda (as the lambda dependence of Sec. 4 requires).
+ * The speeds are the solver's, and dx, dy, dt, tau are shared by all cases of a call.
+ *
+ * Precision: G and its eigenvalues are computed in double-double arithmetic (~106 bits). At the
+ * high-Mach states of Sec. 4 the entries of G carry the cancellation of the 4th-order f^eq, and
+ * the eigenvalues move by O(1) under an FP64 rounding of G. At (2, 30, 0, 1) FP64 results are off
+ * by up to 0.05, while double-double ones agree with 50-digit arithmetic to ~1e-15. */
+typedef struct {
+  double rho, ux, uy, T; /* uniform equilibrium state: rho > 0, T > 0 */
+  double xi_x, xi_y;     /* k_x dx and k_y dy in radians, |xi| <= 8 */
+  double lambda;         /* artificial-viscosity switch held at lambda (>= 0) */
+  int flags;             /* FDLBM_NO_LW | FDLBM_NO_DISP | FDLBM_NO_VISC drop lines II-IV of Eq. 17 */
+  int reserved;          /* must be 0 */
+} fdlbm_vn_case;
+
+/* Per-case status written by fdlbm_vn_spectrum. */
+enum fdlbm_vn_status {
+  FDLBM_VN_OK = 0,
+  FDLBM_VN_BAD_CASE = 1,      /* rho or T not positive, a non-finite field, |xi| > 8, lambda < 0,
+                                 unknown flags or reserved != 0: outputs are NaN */
+  FDLBM_VN_NO_CONVERGENCE = 2 /* the QR iteration exceeded 30 sweeps per eigenvalue: the
+                                 eigenvalues not found are NaN, max_abs is NaN */
+};
+
+/* Eigenvalues of G for n cases, one warp per case.
+ *
+ * cases    n fdlbm_vn_case records, device memory.
+ * n        number of cases, 0 <= n <= 2^31 - 1.
+ * dx, dy, dt, tau   grid spacings, time step, relaxation time (all > 0, finite).
+ * max_abs  n doubles, device memory: max_q |omega_q| per case (the curves of Figs. 2, 4-6 are
+ *          its maximum over the wave numbers).
+ * omega    NULL, or 66 n doubles, device memory: the 33 eigenvalues of case c as (re, im) pairs
+ *          at omega[66 c + 2 q], in no particular order.
+ * G        NULL, or 2178 n doubles, device memory: G of case c, row-major (re, im) pairs at
+ *          G[2178 c + 66 i + 2 j], rounded to FP64 (for checking; costs device bandwidth only).
+ * status   NULL, or n ints, device memory: enum fdlbm_vn_status per case.
+ * cuda_stream  a cudaStream_t or NULL. The call is asynchronous: outputs are valid once the
+ *          stream has passed it. All buffers are caller-owned and must stay valid until then.
+ *
+ * Returns FDLBM_OK, FDLBM_E_ARG (invalid scalar argument or NULL required buffer; nothing is
+ * launched) or FDLBM_E_CUDA (launch failure); the message is in fdlbm_last_error(NULL). */
+int fdlbm_vn_spectrum(const fdlbm_vn_case* cases, long long n, double dx, double dy, double dt, double tau,
+                      double* max_abs, double* omega, double* G, int* status, void* cuda_stream);
+
 /* Release the handle and the memory it owns. NULL-safe. */
 int fdlbm_destroy(fdlbm_t h);
 

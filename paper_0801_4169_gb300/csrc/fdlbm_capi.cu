@@ -84,7 +84,7 @@ Layout layout_of(const fdlbm_config* c) {
 Coeffs make_coeffs(const fdlbm_config* cfg) {
   Coeffs c;
   std::memset(&c, 0, sizeof(c));
-  const double v[4] = {1.0, 1.92, 2.99, 4.49};  // speeds v_1..v_4 (Sec. 4)
+  const double v[4] = {speed(0), speed(1), speed(2), speed(3)};  // speeds v_1..v_4 (Sec. 4)
   for (int k = 0; k < 4; ++k) {
     // Eq. 11 with the cyclic index of Eq. 13
     const double vk2 = v[k] * v[k];

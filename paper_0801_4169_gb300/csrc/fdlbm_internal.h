@@ -17,6 +17,9 @@ namespace fdlbm {
 constexpr int Q = 33;   // Watari-Tsutahara velocity count: rest + 4 speeds x 8 directions (Eq. 1)
 constexpr int NG = 2;   // ghost ring width: Eq. 17 reaches I +- 2 along each axis
 
+// Speeds v_1..v_4 of the four rings (the values of Sec. 4, used for every problem).
+__host__ __device__ constexpr double speed(int k) { return k == 0 ? 1.0 : k == 1 ? 1.92 : k == 2 ? 2.99 : 4.49; }
+
 // Scheme flags (same values as enum fdlbm_flags).
 constexpr int F_NO_LW = 1, F_NO_DISP = 2, F_NO_VISC = 4, F_SWITCH_CONST = 8;
 // Boundary kinds (same values as enum fdlbm_bc).

@@ -100,6 +100,8 @@ def lib():
             "fdlbm_last_error": (ctypes.c_char_p, [_VP]),
             "fdlbm_version": (ctypes.c_char_p, []),
             "fdlbm_step_noalloc": (ctypes.c_int, [cfgp, _VP, _VP, ctypes.c_long, ctypes.POINTER(ctypes.c_long), _VP]),
+            "fdlbm_vn_spectrum": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
             "fdlbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP]),
             "fdlbm_batch_add": (ctypes.c_int, [_VP, _VP]),
             "fdlbm_batch_remove": (ctypes.c_int, [_VP, _VP]),
@@ -429,6 +431,55 @@ def fdlbm_step_noalloc(cfg, f_a, f_b, nsteps, stream=None):
         err.first_bad_step = bad.value
         raise err
     return bad.value
+
+
+# ---- von Neumann analysis (Sec. 4, Eqs. 18-20)
+
+FDLBM_VN_OK, FDLBM_VN_BAD_CASE, FDLBM_VN_NO_CONVERGENCE = 0, 1, 2
+
+# numpy layout of struct fdlbm_vn_case (64 bytes)
+VN_CASE = np.dtype([("rho", "f8"), ("ux", "f8"), ("uy", "f8"), ("T", "f8"), ("xi_x", "f8"), ("xi_y", "f8"),
+                    ("lam", "f8"), ("flags", "i4"), ("reserved", "i4")])
+
+
+def vn_cases(states, xi_x, xi_y, lam, flags=0):
+    """Broadcast per-case arrays into a VN_CASE record array. states: (..., 4) rows (rho, u1, u2, T)."""
+    st = np.asarray(states, dtype=np.float64)
+    shape = np.broadcast_shapes(st.shape[:-1], np.shape(xi_x), np.shape(xi_y), np.shape(lam), np.shape(flags))
+    out = np.zeros(int(np.prod(shape)), dtype=VN_CASE)
+    st = np.broadcast_to(st, shape + (4,)).reshape(-1, 4)
+    for k, name in enumerate(("rho", "ux", "uy", "T")):
+        out[name] = st[:, k]
+    out["xi_x"] = np.broadcast_to(xi_x, shape).ravel()
+    out["xi_y"] = np.broadcast_to(xi_y, shape).ravel()
+    out["lam"] = np.broadcast_to(lam, shape).ravel()
+    out["flags"] = np.broadcast_to(flags, shape).ravel()
+    return out
+
+
+def fdlbm_vn_spectrum(cases, n, dx, dy, dt, tau, max_abs, omega=None, G=None, status=None, stream=None):
+    """Raw call: every array argument is a CUDA tensor (or a device address)."""
+    opt = [None if a is None else _dptr(a) for a in (omega, G, status)]
+    rc = lib().fdlbm_vn_spectrum(_dptr(cases), int(n), float(dx), float(dy), float(dt), float(tau), _dptr(max_abs),
+                                 *opt, _stream_ptr(stream))
+    return _check(None, rc)
+
+
+def vn_spectrum(cases, dx, dy, dt, tau, eigenvalues=False, matrix=False, device="cuda"):
+    """Run fdlbm_vn_spectrum on a VN_CASE array and return host results:
+    (max_abs (n,), status (n,), omega (n, 33) complex or None, G (n, 33, 33) complex or None)."""
+    import torch
+    cases = np.ascontiguousarray(cases, dtype=VN_CASE)
+    n = cases.shape[0]
+    d_cases = torch.from_numpy(cases.view(np.uint8).copy()).to(device)
+    d_max = torch.empty(n, dtype=torch.float64, device=device)
+    d_st = torch.empty(n, dtype=torch.int32, device=device)
+    d_om = torch.empty(66 * n, dtype=torch.float64, device=device) if eigenvalues else None
+    d_G = torch.empty(2178 * n, dtype=torch.float64, device=device) if matrix else None
+    fdlbm_vn_spectrum(d_cases, n, dx, dy, dt, tau, d_max, d_om, d_G, d_st, torch.cuda.current_stream())
+    om = d_om.cpu().numpy().view(np.complex128).reshape(n, 33) if eigenvalues else None
+    G = d_G.cpu().numpy().view(np.complex128).reshape(n, 33, 33) if matrix else None
+    return d_max.cpu().numpy(), d_st.cpu().numpy(), om, G
 
 
 def fdlbm_version():

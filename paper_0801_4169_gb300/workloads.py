@@ -28,6 +28,8 @@ Workloads (all FP64 macros, x fastest, m = 1 so rho = n and p = rho*T):
   serving_requests  seeded Poisson stream of shock-tube solves of mixed size,
                 Mach number, length and precision.
   riemann1d     the 1-D Riemann problems of Sec. 5.1 (Eqs. 21-25) on ny = 1.
+  vn_sec4       the von Neumann sweeps of Sec. 4 (Figs. 2, 4, 5, 6): uniform states,
+                lambda and scheme variants, each over nk wave numbers k dx in (0, pi].
 """
 import math
 from dataclasses import dataclass, field
@@ -231,3 +233,39 @@ def serving_requests(n=512, seed=0, mean_gap_s=0.005, nx_range=(256, 16384), ms_
 def request_workload(req, lam=2.0):
     """The shock-tube solve a serving request describes (upstream flowing at -(Ms - 2) c1)."""
     return shock_tube(nx=req.nx, ny=req.ny, steps=req.steps, Ms=req.Ms, U=max(0.0, req.Ms - 2.0), lam=lam)
+
+
+# flags of the Sec. 4 scheme variants (values of enum fdlbm_flags)
+_NO_LW, _NO_DISP, _NO_VISC = 1, 2, 4
+
+
+def vn_sec4_curves():
+    """The curves of Sec. 4 as (label, (rho, u1, u2, T), lambda, flags). All at dx = dy = 3e-3,
+    dt = tau = 1e-5, speeds (1, 1.92, 2.99, 4.49), wave vector along x.
+
+    Fig. 2: (2, 30, 0, 1), lambda = 0.5, Eq. 17 with line I only, lines I-II, lines I and III, all.
+    Fig. 4: the same state, lambda in {0.05, 0.1, 0.5, 1, 1.8, 2, 3}.
+    Fig. 5: u1 = 5, lambda = 0, T in {1, 5, 15, 25} (rho = 2 kept from Fig. 2).
+    Fig. 6: lambda = 0, u1 from 0 to 30 (steps of 5), T = 1."""
+    base = (2.0, 30.0, 0.0, 1.0)
+    c = [("fig2 line I", base, 0.5, _NO_LW | _NO_DISP | _NO_VISC), ("fig2 lines I-II", base, 0.5, _NO_DISP | _NO_VISC),
+         ("fig2 lines I,III", base, 0.5, _NO_LW | _NO_VISC), ("fig2 all", base, 0.5, 0)]
+    c += [("fig4 lambda=%g" % l, base, l, 0) for l in (0.05, 0.1, 0.5, 1.0, 1.8, 2.0, 3.0)]
+    c += [("fig5 T=%g" % T, (2.0, 5.0, 0.0, float(T)), 0.0, 0) for T in (1, 5, 15, 25)]
+    c += [("fig6 u1=%g" % u, (2.0, float(u), 0.0, 1.0), 0.0, 0) for u in (0, 5, 10, 15, 20, 25, 30)]
+    return c
+
+
+VN_SEC4_GRID = (3e-3, 3e-3, 1e-5, 1e-5)  # dx, dy, dt, tau
+
+
+def vn_sec4_cases(nk=256):
+    """(records, curves, xi): one case per (curve, k dx), curve-major, as plain numbers
+    [rho, u1, u2, T, xi_x, xi_y, lambda, flags] (n, 8)."""
+    curves = vn_sec4_curves()
+    xi = np.linspace(np.pi / nk, np.pi, nk)
+    rows = []
+    for _, st, lam, fl in curves:
+        for x in xi:
+            rows.append([st[0], st[1], st[2], st[3], x, 0.0, lam, fl])
+    return np.array(rows), curves, xi

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_0801_4169_gb300 import fdlbm as F
@@ -78,3 +79,22 @@ def test_null_pointers_rejected():
     with pytest.raises(F.FdlbmError) as ei:
         F._check(None, F.lib().fdlbm_step(None, 1))
     assert ei.value.code == F.FDLBM_E_ARG
+
+
+def test_vn_case_layout_and_argument_checks_without_a_device():
+    assert F.VN_CASE.itemsize == 64  # struct fdlbm_vn_case: 7 doubles + 2 ints
+    assert F.fdlbm_vn_spectrum(0, 0, 1e-3, 1e-3, 1e-5, 1e-5, 0) == 0  # n = 0: nothing to do
+    for bad in (dict(n=-1), dict(dt=0.0), dict(tau=float("nan")), dict(dx=-1.0)):
+        a = dict(n=4, dx=1e-3, dy=1e-3, dt=1e-5, tau=1e-5)
+        a.update(bad)
+        with pytest.raises(F.FdlbmError) as ei:
+            F.fdlbm_vn_spectrum(0, a["n"], a["dx"], a["dy"], a["dt"], a["tau"], 0)
+        assert ei.value.code == F.FDLBM_E_ARG
+    with pytest.raises(F.FdlbmError) as ei:  # NULL cases / max_abs
+        F.fdlbm_vn_spectrum(0, 4, 1e-3, 1e-3, 1e-5, 1e-5, 0)
+    assert ei.value.code == F.FDLBM_E_ARG and "required" in F.fdlbm_last_error(None)
+
+
+def test_vn_cases_broadcast():
+    c = F.vn_cases([(1.0, 2.0, 0.0, 1.0), (2.0, 30.0, 0.0, 1.0)], np.linspace(0.1, 1.0, 5)[:, None], 0.0, 0.5)
+    assert c.shape == (10,) and np.all(c["reserved"] == 0) and c["ux"][1] == 30.0 and c["xi_x"][2] == c["xi_x"][3]
