@@ -249,35 +249,104 @@ __device__ __forceinline__ Mom node_moments(const double* __restrict__ f, long l
   return combine_rings(ld(f + off), S, X, Y, c);
 }
 
-// FP32 storage: the 33 values are widened to FP64 exactly, then summed in FP64. The integer path
-// serves normal numbers; a node holding a zero, subnormal or non-finite value takes the hardware
-// conversion (a separate branch, so the common path issues no FP64 conversions).
-__device__ __forceinline__ Mom moments_from(const float (&x)[Q], const Coeffs& c, bool hw) {
-  double S[4], X[4], Y[4];
+// FP32 storage: the moments are summed exactly in 64-bit fixed point on the integer pipe, which
+// replaces ~55 of the ~80 FP64 operations of the FP64 summation.
+//  - Scale: with e* the largest biased exponent of the node's 33 values (subnormals count as 1), a
+//    value x becomes the integer trunc(x 2^(181 - e*)): its 24-bit significand shifted so that the
+//    largest value's top bit lands on bit 54. A value below 2^-55 of the largest loses the bits
+//    under the unit; the error is below 2^-54 of the largest value per term, less than one
+//    rounding of an FP64 sum. Any sum of 33 terms stays below 2^61.
+//  - Per ring, the integers S = sum g, AX = g7 - g3, DX = (g0 - g4) + (g6 - g2), AY = g1 - g5,
+//    DY = (g0 - g4) - (g6 - g2) are exact, as is N = f_0 + sum_k S_k. They are converted to FP64 by
+//    integer bit operations with one rounding each (fix_to_f64). In FP64:
+//      n = N,  X_k = fma(s, DX_k, AX_k),  Y_k = fma(s, DY_k, AY_k),
+//    and jx, jy, sum |v|^2 f follow the pairwise ring tree of combine_rings.
+//  - Integer sums are associative, so the ring-parallel kernel, which adds its lanes' integers in
+//    another order, forms bit-identical moments.
+//  - A node holding an infinity or NaN (biased exponent 255) gets NaN moments, which the health
+//    check reports.
+__device__ __forceinline__ int f32_exp1(float x) {
+  const int e = (int)((__float_as_uint(x) >> 23) & 0xffu);
+  return e ? e : 1;
+}
+__device__ __forceinline__ long long to_fix(float x, int emax) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
+  const int sh = emax - (e ? (int)e : 1);  // 0 .. 253 for finite values
+  const unsigned long long t = sh < 64 ? (((unsigned long long)m << 31) >> sh) : 0ull;
+  return (u >> 31) ? -(long long)t : (long long)t;
+}
+// V * 2^e2, rounded to nearest even, built from the integer's bits (|V| < 2^62, normal result).
+__device__ __forceinline__ double fix_to_f64(long long V, int e2) {
+  if (V == 0) return 0.0;
+  const unsigned long long sgn = V < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long U = V < 0 ? (unsigned long long)(-V) : (unsigned long long)V;
+  const int lz = __clzll((long long)U);
+  U <<= lz;  // leading one at bit 63
+  unsigned long long M = U >> 11;
+  const unsigned rem = (unsigned)(U & 0x7ffull);
+  M += (unsigned long long)((rem > 0x400u) | ((rem == 0x400u) & (unsigned)(M & 1ull)));
+  const unsigned long long E = (unsigned long long)(63 - lz + e2 + 1023);  // biased exponent
+  // the significand's leading one (bit 52) adds the last 1 to the exponent field; a rounding
+  // carry into bit 53 adds one more, which is the correct result
+  return __longlong_as_double((long long)(sgn | (((E - 1ull) << 52) + M)));
+}
+struct RingFix {
+  long long S, AX, DX, AY, DY;
+};
+__device__ __forceinline__ RingFix ring_fix(const float (&x)[8], int emax) {
+  long long g[8];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    double g[8];
-#pragma unroll
-    for (int d = 0; d < 8; ++d) g[d] = hw ? (double)x[1 + 8 * k + d] : f32_to_f64_bits(x[1 + 8 * k + d]);
-    ring_sums(g, S[k], X[k], Y[k]);
-  }
-  return combine_rings(hw ? (double)x[0] : f32_to_f64_bits(x[0]), S, X, Y, c);
+  for (int d = 0; d < 8; ++d) g[d] = to_fix(x[d], emax);
+  RingFix r;
+  r.S = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]));
+  const long long a = g[0] - g[4], b = g[6] - g[2];
+  r.AX = g[7] - g[3];
+  r.DX = a + b;
+  r.AY = g[1] - g[5];
+  r.DY = a - b;
+  return r;
+}
+__device__ __forceinline__ void ring_from_fix(const RingFix& r, int e2, double& S, double& X, double& Y) {
+  S = fix_to_f64(r.S, e2);
+  X = fma(kS, fix_to_f64(r.DX, e2), fix_to_f64(r.AX, e2));
+  Y = fma(kS, fix_to_f64(r.DY, e2), fix_to_f64(r.AY, e2));
+}
+__device__ __forceinline__ Mom nan_moments() {
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  return Mom{nan, nan, nan, nan};
 }
 
 __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long long plane, long long off,
                                             const Coeffs& c) {
   float x[Q];
-  bool special = false;
+  int emax = 1;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     x[q] = ld(f + (long long)q * plane + off);
-    special |= f32_special(x[q]);
+    emax = max(emax, f32_exp1(x[q]));
   }
-  if (!special) return moments_from(x, c, false);
-  return moments_from(x, c, true);
+  if (emax == 255) return nan_moments();
+  const int e2 = emax - 181;
+  long long N = to_fix(x[0], emax);
+  double S[4], X[4], Y[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float g[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) g[d] = x[1 + 8 * k + d];
+    const RingFix r = ring_fix(g, emax);
+    N += r.S;
+    ring_from_fix(r, e2, S[k], X[k], Y[k]);
+  }
+  Mom m = combine_rings(0.0, S, X, Y, c);
+  m.n = fix_to_f64(N, e2);
+  return m;
 }
 
-// One ring of a node (ring-parallel kernel): S, X, Y of ring k, and f_0 (read by every lane).
+// One ring of a node (ring-parallel kernel, FP64 storage): S, X, Y of ring k, and f_0 (read by
+// every lane).
 __device__ __forceinline__ void ring_of_node(const double* __restrict__ f, long long plane, long long off, int k,
                                              double& f0, double& S, double& X, double& Y) {
   double g[8];
@@ -286,27 +355,41 @@ __device__ __forceinline__ void ring_of_node(const double* __restrict__ f, long 
   f0 = ld(f + off);
   ring_sums(g, S, X, Y);
 }
-__device__ __forceinline__ void ring_of_node(const float* __restrict__ f, long long plane, long long off, int k,
-                                             double& f0, double& S, double& X, double& Y) {
+
+// Ring-parallel kernel: lane r of a quad (r = 0..3) gets S, X, Y of ring r of the quad's node and
+// the node's n, which every lane of the quad ends with. All four lanes must call it together.
+__device__ __forceinline__ void quad_ring(const double* __restrict__ f, long long plane, long long off, int r,
+                                          double& S, double& X, double& Y, double& n) {
+  double f0;
+  ring_of_node(f, plane, off, r, f0, S, X, Y);
+  // n = ((f_0 + S_0) + S_1) + (S_2 + S_3), the tree of combine_rings
+  const double pn = (r == 0) ? f0 + S : S;
+  const double n2 = pn + __shfl_xor_sync(0xffffffffu, pn, 1);
+  n = n2 + __shfl_xor_sync(0xffffffffu, n2, 2);
+}
+__device__ __forceinline__ void quad_ring(const float* __restrict__ f, long long plane, long long off, int r,
+                                          double& S, double& X, double& Y, double& n) {
   float x[8];
   const float x0 = ld(f + off);
-  bool special = f32_special(x0);
+  int emax = f32_exp1(x0);
 #pragma unroll
   for (int d = 0; d < 8; ++d) {
-    x[d] = ld(f + (long long)(1 + 8 * k + d) * plane + off);
-    special |= f32_special(x[d]);
+    x[d] = ld(f + (long long)(1 + 8 * r + d) * plane + off);
+    emax = max(emax, f32_exp1(x[d]));
   }
-  double g[8];
-  if (!special) {
-#pragma unroll
-    for (int d = 0; d < 8; ++d) g[d] = f32_to_f64_bits(x[d]);
-    f0 = f32_to_f64_bits(x0);
-  } else {
-#pragma unroll
-    for (int d = 0; d < 8; ++d) g[d] = (double)x[d];
-    f0 = (double)x0;
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
+  const RingFix rf = ring_fix(x, emax);
+  long long N = rf.S + (r == 0 ? to_fix(x0, emax) : 0ll);
+  N += __shfl_xor_sync(0xffffffffu, N, 1);
+  N += __shfl_xor_sync(0xffffffffu, N, 2);
+  const int e2 = emax - 181;
+  ring_from_fix(rf, e2, S, X, Y);
+  n = fix_to_f64(N, e2);
+  if (emax == 255) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    S = X = Y = n = nan;
   }
-  ring_sums(g, S, X, Y);
 }
 
 // (n, ux, uy, T, P) from the sums; T = (sum |v|^2 f)/(2n) - |u|^2/2  (Eq. 5 with P = nT).
@@ -688,26 +771,23 @@ __global__ void __launch_bounds__(4 * TW * TH) k_step_rp(const S* __restrict__ f
         inslot && ((inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny)));
     const int cx = min(max(gx, -1), g.nx), cy = min(max(gy, -1), g.ny);
     const long long off = (long long)(cy + NG) * g.pitch + (cx + NG);
-    double f0, Sr, Xr, Yr;
-    ring_of_node(f, g.plane, off, r, f0, Sr, Xr, Yr);
-    // stage 1 (lanes r, r^1): n pair = (f0 + S_0) + S_1 or S_2 + S_3; j pair = fma(v_e, X_e, v_o X_o)
+    double Sr, Xr, Yr, nq;
+    quad_ring(f, g.plane, off, r, Sr, Xr, Yr, nq);
+    // stage 1 (lanes r, r^1): j pair = fma(v_e, X_e, v_o X_o)
     const bool even = (r & 1) == 0;
-    const double pn = (r == 0) ? f0 + Sr : Sr;
     const double prodx = c.v[r] * Xr, prody = c.v[r] * Yr, prode = c.v2[r] * Sr;
     // the even lane sends its X (Y, S), the odd lane its product v X; each then forms
     // fma(v_even, X_even, v_odd X_odd) from identical operands
-    const double o_pn = __shfl_xor_sync(FULL, pn, 1);
     const double o_x = __shfl_xor_sync(FULL, even ? Xr : prodx, 1);
     const double o_y = __shfl_xor_sync(FULL, even ? Yr : prody, 1);
     const double o_e = __shfl_xor_sync(FULL, even ? Sr : prode, 1);
     const int re = r & 2;  // the even lane of the pair
-    double n2 = pn + o_pn;
     double jx2 = even ? fma(c.v[re], Xr, o_x) : fma(c.v[re], o_x, prodx);
     double jy2 = even ? fma(c.v[re], Yr, o_y) : fma(c.v[re], o_y, prody);
     double e22 = even ? fma(c.v2[re], Sr, o_e) : fma(c.v2[re], o_e, prode);
     // stage 2 (pairs 01 and 23): commutative sums, equal in all four lanes
     Mom m;
-    m.n = n2 + __shfl_xor_sync(FULL, n2, 2);
+    m.n = nq;
     m.jx = jx2 + __shfl_xor_sync(FULL, jx2, 2);
     m.jy = jy2 + __shfl_xor_sync(FULL, jy2, 2);
     m.e2 = e22 + __shfl_xor_sync(FULL, e22, 2);
