@@ -76,19 +76,21 @@ struct BatchMember {
 
 // Tile shape (width, height) of a launch variant.
 inline void variant_tile(int v, int* tw, int* th) {
-  static const int W[8] = {32, 32, 32, 16, 64, 32, 32, 32}, H[8] = {4, 8, 16, 4, 8, 32, 16, 32};
+  static const int W[8] = {32, 32, 32, 16, 64, 32, 32, 32}, H[8] = {4, 8, 16, 4, 8, 32, 24, 28};
   *tw = W[v];
   *th = H[v];
 }
 
-// Launch configuration of the fused step: tile of TW x TH nodes per CTA. Variants 0-5 cap the
-// registers at 128 per thread (2-4 CTAs per SM); the _R variants leave the allocation free
-// (one 256-thread CTA per SM, no spills).
+// Launch configuration of the fused step: tile of TW x TH nodes per CTA, registers capped at 128
+// per thread (2-4 CTAs per SM). Phase 1 computes the moments of the tile and its 1-node ring,
+// (TW+2)(TH+2) - 4 nodes, in rounds of one node per thread. 32 x 24 and 32 x 28 on 128 threads
+// fill 98-99 % of their rounds (32 x 16 on 256 threads: 79 %); which shape is fastest depends on
+// the precision and the grid, and the autotuner measures it.
 // V_RP* are the ring-parallel variants (four lanes per node) for small grids; batches use the
 // tile variants only (V_TILE_COUNT).
 enum StepVariant {
-  V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_T32x32 = 5, V_T32x16_R = 6,
-  V_T32x32_R = 7, V_TILE_COUNT = 8, V_RP16x4 = 8, V_RP8x4 = 9, V_COUNT = 10
+  V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_T32x32 = 5, V_T32x24 = 6,
+  V_T32x28 = 7, V_TILE_COUNT = 8, V_RP16x4 = 8, V_RP8x4 = 9, V_COUNT = 10
 };
 
 // Kernel launchers (fdlbm_aux.cu, fdlbm_step_f32.cu, fdlbm_step_f64.cu). All return

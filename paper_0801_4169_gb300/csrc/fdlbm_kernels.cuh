@@ -991,8 +991,8 @@ cudaError_t launch_batch_v(int variant, const BatchMember* mem, int nmem, long l
     case V_T16x4: return launch_batch_t<S, 16, 4, 1, 1>(mem, nmem, tiles, step, c, s);
     case V_T64x8: return launch_batch_t<S, 64, 4, 2, 2>(mem, nmem, tiles, step, c, s);
     case V_T32x32: return launch_batch_t<S, 32, 8, 4, 2>(mem, nmem, tiles, step, c, s);
-    case V_T32x16_R: return launch_batch_t<S, 32, 8, 2, 1>(mem, nmem, tiles, step, c, s);
-    case V_T32x32_R: return launch_batch_t<S, 32, 8, 4, 1>(mem, nmem, tiles, step, c, s);
+    case V_T32x24: return launch_batch_t<S, 32, 4, 6, 4>(mem, nmem, tiles, step, c, s);
+    case V_T32x28: return launch_batch_t<S, 32, 4, 7, 4>(mem, nmem, tiles, step, c, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1016,8 +1016,8 @@ cudaError_t launch_step_v(int variant, const void* f, void* fn, const Grid& g, c
     case V_T16x4: return launch_step_t<S, 16, 4, 1, 1>(f, fn, g, c, health, s);
     case V_T64x8: return launch_step_t<S, 64, 4, 2, 2>(f, fn, g, c, health, s);
     case V_T32x32: return launch_step_t<S, 32, 8, 4, 2>(f, fn, g, c, health, s);
-    case V_T32x16_R: return launch_step_t<S, 32, 8, 2, 1>(f, fn, g, c, health, s);
-    case V_T32x32_R: return launch_step_t<S, 32, 8, 4, 1>(f, fn, g, c, health, s);
+    case V_T32x24: return launch_step_t<S, 32, 4, 6, 4>(f, fn, g, c, health, s);
+    case V_T32x28: return launch_step_t<S, 32, 4, 7, 4>(f, fn, g, c, health, s);
     default: return cudaErrorInvalidValue;
   }
 }
