@@ -100,6 +100,7 @@ Coeffs make_coeffs(const fdlbm_config* cfg) {
     c.v2[k] = vk2;
     c.v3_6[k] = vk2 * v[k] / 6.0;
     c.v4_24[k] = vk2 * vk2 / 24.0;
+    c.v2h[k] = 0.5 * vk2;
   }
   const double kk[2] = {cfg->dt / cfg->dx, cfg->dt / cfg->dy};
   const double s = std::sqrt(0.5);
@@ -137,7 +138,10 @@ Coeffs make_coeffs(const fdlbm_config* cfg) {
 
 int default_variant(const fdlbm_config* c) {
   const long long sites = (long long)c->nx * c->ny;
-  if (sites <= 65536) return V_RP16x4;  // small grids: latency-bound, four lanes per node
+  // Small grids are latency-bound: four lanes per node win up to a few thousand sites (400 x 4:
+  // 16 us per step against 32 us for the tiles), and lose by 1.3x at 16 000 sites, where the
+  // tiles have reached their latency floor while the ring-parallel launch is throughput-bound.
+  if (sites <= 6144) return V_RP8x4;
   if (c->ny <= 4) return V_T32x4;
   if (sites < 200000) return V_T32x8;
   return V_T32x16;

@@ -48,6 +48,7 @@ struct Coeffs {
   double v2[4];       // v_k^2
   double v3_6[4];     // v_k^3 / 6
   double v4_24[4];    // v_k^4 / 24
+  double v2h[4];      // v_k^2 / 2
   // Eq. 17 stencil weights without line IV, for axis a (0 = x, 1 = y), ring k, class c (0 = the
   // two axis-aligned directions, |c| = v_k dt/dr_a; 1 = the four diagonals, |c| = v_k dt/(sqrt2 dr_a)),
   // for the direction with positive c. The negative direction swaps W1/Wm1 and negates D.

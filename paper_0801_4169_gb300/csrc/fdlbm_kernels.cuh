@@ -416,7 +416,7 @@ __device__ __forceinline__ bool macro_ok(const Macro& o) {
 // ---------------------------------------------------------------------------------------------
 // Equilibrium constants of one node (Eqs. 10-13), with dt/tau folded in (rn = r * n).
 struct EqSite {
-  double rn, A0, A1, A2;   // A0 = 1 - b + b^2/2, A1 = 1 - b, A2 = (1-b)/2, b = |u|^2/(2 theta)
+  double rn, A0, A1;       // A0 = 1 - b + b^2/2, A1 = 1 - b, b = |u|^2/(2 theta)
   double p[4];             // projections (e.u)/theta for d = 7 (x), 0 (diag), 1 (y), 2 (anti-diag)
   double x[4];             // p^2
   double F[4];             // F_1..F_4
@@ -437,7 +437,6 @@ __device__ __forceinline__ EqSite eq_site(double n, double ux, double uy, double
   const double b = 0.5 * fma(ux, ux, uy * uy) * ith;
   e.A1 = 1.0 - b;
   e.A0 = fma(0.5 * b, b, e.A1);
-  e.A2 = 0.5 * e.A1;
   double sF = 0.0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -449,7 +448,8 @@ __device__ __forceinline__ EqSite eq_site(double n, double ux, double uy, double
   return e;
 }
 
-// Per-ring constants alpha..eps (times r n F_k).
+// Per-ring constants alpha..eps (times r n F_k), 7 FP64 ops per ring: with t = r n F_k (1 - b),
+//   alpha = r n F_k A0,  beta = t v_k^2/2,  gamma = r n F_k v_k^4/24,  delta = t v_k,  eps = r n F_k v_k^3/6.
 struct EqRing {
   double al, be, ga, de, ep;
 };
@@ -458,10 +458,11 @@ __device__ __forceinline__ EqRing eq_ring(const EqSite& e, int k, const Coeffs& 
   // select, not e.F[k]: k may be a run-time ring index (ring-parallel kernel)
   const double Fk = k == 0 ? e.F[0] : k == 1 ? e.F[1] : k == 2 ? e.F[2] : e.F[3];
   const double nF = e.rn * Fk;
+  const double t = nF * e.A1;
   r.al = nF * e.A0;
-  r.be = nF * (e.A2 * c.v2[k]);
+  r.be = t * c.v2h[k];
   r.ga = nF * c.v4_24[k];
-  r.de = nF * (e.A1 * c.v[k]);
+  r.de = t * c.v[k];
   r.ep = nF * c.v3_6[k];
   return r;
 }

@@ -185,6 +185,9 @@ RIEMANN1D = {
     "colella": ((1.0, 0.0, 0.0, 1000.0), (1.0, 0.0, 0.0, 0.01), 3e-3, 1e-5, 1e-5, 20.0, 0.05),
     "collision": ((5.99924, 19.5975, 0.0, 76.8254), (5.99242, -6.19633, 0.0, 7.69222), 2e-3, 1e-5, 1e-5,
                   1.0, 0.12),
+    # Sec. 4, Fig. 3: the dispersion on/off tube, "otherwise as Fig. 2" (dx = 3e-3, dt = tau = 1e-5).
+    # The paper gives no end time; 0.03 keeps both shocks inside 400 nodes.
+    "fig3": ((10.0, 10.0, 0.0, 5.0), (10.0, 0.0, 0.0, 5.0), 3e-3, 1e-5, 1e-5, 2.0, 0.03),
 }
 
 
