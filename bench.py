@@ -49,7 +49,7 @@ BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4}
 # FP64 instructions (DADD + DFMA + DMUL) per amplification-matrix spectrum of the von Neumann
 # tool on the Sec. 4 sweep: ncu thread-level counts of k_vn divided by the cases. They include the
 # rotation parameters every lane computes alike, so they bound the algorithmic work from above.
-FP64_OPS_PER_VN_MATRIX = 16.46e6
+FP64_OPS_PER_VN_MATRIX = 15.48e6
 # FP64 issue peak: 2 instructions per clock per SM, i.e. the nominal 1.25 TFLOP/s at 2.07 GHz
 # (ncu's pct-of-peak for the FP64 pipe agrees with it).
 FP64_OPS_PER_CLK_SM = 2.0

@@ -118,30 +118,88 @@ __device__ cdd wilkinson(const cdd& a, const cdd& b, const cdd& c, const cdd& d)
 }
 __device__ __forceinline__ double l1_hi(const cdd& z) { return fabs(z.re.hi) + fabs(z.im.hi); }
 
-// Rotation acting on rows (k, k+1): [c s; -conj(s) c], c real, chosen to zero the lower entry.
+// Plane rotation of rows (k, k+1): U = [a b; -conj(b) conj(a)] with a = conj(x)/r, b = conj(y)/r,
+// r = sqrt(|x|^2 + |y|^2). U is unitary, maps (x, y) to (r, 0), and needs one reciprocal
+// square root. Applied from the left to rows k, k+1, and as U^H from the right to columns k, k+1.
 struct Rot {
-  dd_t c;
-  cdd s;
+  cdd a, b;
 };
 __device__ Rot givens(const cdd& x, const cdd& y) {
-  const dd_t ax2 = dd::cabs2(x), ay2 = dd::cabs2(y);
-  const dd_t r2 = dd::add(ax2, ay2);
+  const dd_t r2 = dd::add(dd::cabs2(x), dd::cabs2(y));
   Rot g;
   if (r2.hi == 0.0) {
-    g.c = dd::make(1.0);
-    g.s = {dd::make(0.0), dd::make(0.0)};
+    g.a = {dd::make(1.0), dd::make(0.0)};
+    g.b = {dd::make(0.0), dd::make(0.0)};
     return g;
   }
   const dd_t rinv = dd::rsqrt(r2);
-  if (ax2.hi == 0.0) {  // x = 0: swap rows, s = conj(y)/|y|
-    g.c = dd::make(0.0);
-    g.s = dd::cmul(dd::cconj(y), rinv);
-    return g;
-  }
-  const dd_t t = dd::mul(dd::rsqrt(ax2), rinv);  // 1 / (|x| r)
-  g.c = dd::mul(ax2, t);                         // |x| / r
-  g.s = dd::cmul(dd::cmulc(y, x), t);            // (x/|x|) conj(y) / r
+  g.a = dd::cmul(dd::cconj(x), rinv);
+  g.b = dd::cmul(dd::cconj(y), rinv);
   return g;
+}
+// One output element of a rotation, one lane each: lane parity picks the output row (left
+// product: new_k = a X + b Y, new_k+1 = -conj(b) X + conj(a) Y) or column (right product by U^H:
+// new_k = conj(a) P + conj(b) Q, new_k+1 = -b P + a Q). Both lanes of a pair read the same two
+// inputs, so the warp reads everything before anyone writes.
+__device__ __forceinline__ void rot_coeffs_left(const Rot& g, bool second, cdd* al, cdd* be) {
+  if (!second) {
+    *al = g.a;
+    *be = g.b;
+  } else {
+    *al = dd::cconj(g.b);
+    al->re = dd::neg(al->re);
+    al->im = dd::neg(al->im);
+    *be = dd::cconj(g.a);
+  }
+}
+__device__ __forceinline__ void rot_coeffs_right(const Rot& g, bool second, cdd* al, cdd* be) {
+  if (!second) {
+    *al = dd::cconj(g.a);
+    *be = dd::cconj(g.b);
+  } else {
+    *al = {dd::neg(g.b.re), dd::neg(g.b.im)};
+    *be = g.a;
+  }
+}
+// rows (k, k+1) over columns j0 .. j1
+__device__ __forceinline__ void rotate_rows(VnShared& S, const Rot& g, int k, int j0, int j1, int lane) {
+  cdd al, be;
+  rot_coeffs_left(g, lane & 1, &al, &be);
+  const int row = k + (lane & 1);
+  for (int base = j0; base <= j1; base += 16) {
+    const int j = base + (lane >> 1);
+    const bool act = j <= j1;
+    cdd X, Y;
+    if (act) {
+      X = ldA(S, k, j);
+      Y = ldA(S, k + 1, j);
+    }
+    __syncwarp();
+    if (act) {
+      cdd out = dd::cadd(dd::cmul(al, X), dd::cmul(be, Y));
+      if (row == k + 1 && j == k) out = cdd{dd::make(0.0), dd::make(0.0)};  // the zeroed entry, exactly
+      stA(S, row, j, out);
+    }
+    __syncwarp();
+  }
+}
+// columns (k, k+1) over rows i0 .. i1, by U^H from the right
+__device__ __forceinline__ void rotate_cols(VnShared& S, const Rot& g, int k, int i0, int i1, int lane) {
+  cdd al, be;
+  rot_coeffs_right(g, lane & 1, &al, &be);
+  const int col = k + (lane & 1);
+  for (int base = i0; base <= i1; base += 16) {
+    const int i = base + (lane >> 1);
+    const bool act = i <= i1;
+    cdd P, Qv;
+    if (act) {
+      P = ldA(S, i, k);
+      Qv = ldA(S, i, k + 1);
+    }
+    __syncwarp();
+    if (act) stA(S, i, col, dd::cadd(dd::cmul(P, al), dd::cmul(Qv, be)));
+    __syncwarp();
+  }
 }
 
 __global__ void __launch_bounds__(32) k_vn(const fdlbm_vn_case* __restrict__ cases, double dx, double dy,
@@ -324,8 +382,10 @@ __global__ void __launch_bounds__(32) k_vn(const fdlbm_vn_case* __restrict__ cas
     // column k becomes (alpha, 0, ..., 0) below the diagonal
     if (lane < m) stA(S, k + 1 + lane, k, lane == 0 ? alpha : cdd{dd::make(0.0), dd::make(0.0)});
     __syncwarp();
-    // right: all rows (lane -> row, lane 0 also row 32), A -= (beta A v) v^H
-    for (int i = lane; i < N; i += 32) {
+    // right: A -= (beta A v) v^H. Rows 0..31 one per lane; row 32 by the whole warp (lane j takes
+    // column k+1+j, the dot product is a warp sum), so no lane runs a second pass alone.
+    {
+      const int i = lane;
       cdd w = {dd::make(0.0), dd::make(0.0)};
       for (int j = 0; j < m; ++j) {
         const cdd vj = {ldd(S.v[2 * j]), ldd(S.v[2 * j + 1])};
@@ -336,6 +396,15 @@ __global__ void __launch_bounds__(32) k_vn(const fdlbm_vn_case* __restrict__ cas
         const cdd vj = {ldd(S.v[2 * j]), ldd(S.v[2 * j + 1])};
         stA(S, i, k + 1 + j, dd::csub(ldA(S, i, k + 1 + j), dd::cmul(w, dd::cconj(vj))));
       }
+    }
+    {
+      cdd t = {dd::make(0.0), dd::make(0.0)}, vl = {dd::make(0.0), dd::make(0.0)};
+      if (lane < m) {
+        vl = {ldd(S.v[2 * lane]), ldd(S.v[2 * lane + 1])};
+        t = dd::cmul(ldA(S, N - 1, k + 1 + lane), vl);
+      }
+      const cdd w = dd::cmul(cdd{warp_sum(t.re), warp_sum(t.im)}, beta);
+      if (lane < m) stA(S, N - 1, k + 1 + lane, dd::csub(ldA(S, N - 1, k + 1 + lane), dd::cmul(w, dd::cconj(vl))));
     }
     __syncwarp();
   }
@@ -350,11 +419,18 @@ __global__ void __launch_bounds__(32) k_vn(const fdlbm_vn_case* __restrict__ cas
   dd_t maxabs2 = dd::make(0.0);
   int st = FDLBM_VN_OK, hi = N - 1, its = 0, sweeps = 0;
   while (hi >= 0) {
-    int l = hi;
-    for (; l > 0; --l) {
-      const double sub = l1_hi(ldA(S, l, l - 1));
-      const double tst = l1_hi(ldA(S, l - 1, l - 1)) + l1_hi(ldA(S, l, l));
-      if (sub <= eps * tst || sub <= floor_abs) break;
+    // the largest l <= hi whose subdiagonal entry is negligible (0 if none), lane l-1 testing l
+    int l;
+    {
+      const int lt = lane + 1;
+      bool negl = false;
+      if (lt <= hi) {
+        const double sub = l1_hi(ldA(S, lt, lt - 1));
+        const double tst = l1_hi(ldA(S, lt - 1, lt - 1)) + l1_hi(ldA(S, lt, lt));
+        negl = sub <= eps * tst || sub <= floor_abs;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, negl);
+      l = m ? 32 - __clz((int)m) : 0;
     }
     const int lo = l;
     if (lo >= hi - 1) {  // a 1 x 1 or 2 x 2 block splits off: its eigenvalues directly
@@ -397,33 +473,11 @@ __global__ void __launch_bounds__(32) k_vn(const fdlbm_vn_case* __restrict__ cas
     for (int k = lo; k < hi; ++k) {
       const Rot g = givens(ldA(S, k, k), ldA(S, k + 1, k));
       __syncwarp();
-      // left rotation of rows k, k+1 over columns k .. hi
-      for (int j = k + lane; j <= hi; j += 32) {
-        const cdd X = ldA(S, k, j), Y = ldA(S, k + 1, j);
-        stA(S, k, j, dd::cadd(dd::cmul(X, g.c), dd::cmul(g.s, Y)));
-        if (j == k)
-          stA(S, k + 1, j, cdd{dd::make(0.0), dd::make(0.0)});
-        else
-          stA(S, k + 1, j, dd::csub(dd::cmul(Y, g.c), dd::cmulc(g.s, X)));
-      }
-      __syncwarp();
-      // right rotation k-1 of columns k-1, k over rows lo .. k: [P Q] -> [c P + conj(s) Q, -s P + c Q]
-      if (k > lo) {
-        for (int i = lo + lane; i <= k; i += 32) {
-          const cdd P = ldA(S, i, k - 1), Qv = ldA(S, i, k);
-          stA(S, i, k - 1, dd::cadd(dd::cmul(P, prev.c), dd::cmulc(prev.s, Qv)));
-          stA(S, i, k, dd::csub(dd::cmul(Qv, prev.c), dd::cmul(prev.s, P)));
-        }
-        __syncwarp();
-      }
+      rotate_rows(S, g, k, k, hi, lane);                // left rotation of rows k, k+1
+      if (k > lo) rotate_cols(S, prev, k - 1, lo, k, lane);  // right rotation k-1 over rows lo..k
       prev = g;
     }
-    for (int i = lo + lane; i <= hi; i += 32) {
-      const cdd P = ldA(S, i, hi - 1), Qv = ldA(S, i, hi);
-      stA(S, i, hi - 1, dd::cadd(dd::cmul(P, prev.c), dd::cmulc(prev.s, Qv)));
-      stA(S, i, hi, dd::csub(dd::cmul(Qv, prev.c), dd::cmul(prev.s, P)));
-    }
-    __syncwarp();
+    rotate_cols(S, prev, hi - 1, lo, hi, lane);
     for (int q = lo + lane; q <= hi; q += 32) stA(S, q, q, dd::cadd(ldA(S, q, q), mu));
     __syncwarp();
   }

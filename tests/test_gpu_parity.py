@@ -283,3 +283,32 @@ def test_full_size_sampled_one_step_parity(name, prec):
                   max(_kappa(win[:, k, 2]) for k in (0, 1, 3, 4)))
         assert np.max(np.abs(got - ref)) <= c * eps * kap * scale, ((i, j), kap)
     assert s.sync() == 0
+
+
+@pytest.mark.parametrize("prec", [F.FDLBM_FP32_STORE, F.FDLBM_FP64])
+def test_beyond_2e31_elements_per_buffer(prec):
+    """8192^2 nodes: each buffer holds 33 x 8196 x 8224 = 2.2e9 elements, beyond 2^31, so every
+    plane offset past the 31st velocity and every flat index above 2^31 takes the 64-bit path
+    (17.8 GB with FP32 storage, 35.6 GB with FP64). One step from the initial state agrees with
+    the oracle's update of sampled nodes: the four corners, the last row and column, random nodes."""
+    w = W.riemann4q(n=8192, steps=1)
+    s = F.Solver.from_workload(w, prec)
+    n = w.nx
+    rng = np.random.default_rng(11)
+    nodes = [(2, 2), (n - 3, 2), (2, n - 3), (n - 3, n - 3), (n // 2, n - 3), (n - 3, n // 2)]
+    nodes += [(int(rng.integers(2, n - 2)), int(rng.integers(2, n - 2))) for _ in range(10)]
+    wins = [s.get_f_region(i - 2, j - 2, 5, 5) for (i, j) in nodes]
+    s.step(1)
+    eps = np.finfo(np.float64).eps if prec == F.FDLBM_FP64 else float(np.finfo(np.float32).eps)
+    c = 512 if prec == F.FDLBM_FP64 else 4
+    for (i, j), win in zip(nodes, wins):
+        got = s.get_f_region(i, j, 1, 1)[:, 0, 0]
+        ref = _window_update(win, w)
+        kap = max(_kappa(win[:, 2, 2]), max(_kappa(win[:, 2, k]) for k in (0, 1, 3, 4)),
+                  max(_kappa(win[:, k, 2]) for k in (0, 1, 3, 4)))
+        assert np.max(np.abs(got - ref)) <= c * eps * kap * np.abs(win).max(), ((i, j), kap)
+    # the moments read back at the far corner equal the oracle's moments of the stored f
+    rho = s.get_macro(check=True)[0]
+    f = s.get_f_region(n - 1, n - 1, 1, 1)[:, 0, 0].astype(np.float64)
+    assert abs(rho[n - 1, n - 1] - f.sum()) <= 64 * np.finfo(np.float64).eps * np.abs(f).sum()
+    s.close()
