@@ -43,7 +43,12 @@ sys.path.insert(0, ROOT)
 # FP64 arithmetic instructions (DADD + DFMA + DMUL) per site update of the fused step, without
 # the moments of the tile ring (ncu counts of the kernel minus that halo work; see profiles/).
 # FP32 storage sums its moments in 64-bit fixed point on the integer pipe, hence the lower count.
-FP64_OPS_PER_LUP = {"fp64": 579, "fp32": 171}
+FP64_OPS_PER_LUP = {"fp64": 577, "fp32": 166}
+# DRAM bytes (read + write) per site update of one k_step launch, by (precision, tile variant):
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this bench's 4096^2 workload
+# (single-pass capture), divided by the sites. Reported as roofline.traffic when the autotuner
+# picks the captured variant, else null.
+TRAFFIC_B_PER_SITE = {("fp32", 2): 264.1, ("fp64", 7): 842.8}
 # Minimum HBM bytes per site update: read and write all 33 f once.
 BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4}
 # FP64 instructions (DADD + DFMA + DMUL) per amplification-matrix spectrum of the von Neumann
@@ -388,6 +393,8 @@ def main():
     site_rate = w.nx * w.ny / (per_launch_ms * 1e-3)
     achieved = FP64_OPS_PER_LUP[prec_name] * site_rate / 1e9
     hbm_gbs = BYTES_PER_LUP[prec_name] * site_rate / 1e9
+    tb = TRAFFIC_B_PER_SITE.get((prec_name, variant)) if (w.nx, w.ny) == (4096, 4096) else None
+    traffic = tb * w.nx * w.ny if tb else None
 
     line = {
         "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
@@ -402,7 +409,8 @@ def main():
                    "status": status, "parallelism": "replicas%d" % world},
         "roofline": {"bound": "alu", "kernel": "k_step (fused step)", "achieved": achieved,
                      "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak,
-                     "traffic": None, "peak_derivation": "2 FP64 ops/clk/SM (nominal 1.25 TFLOP/s) x 152 SMs x %.0f MHz sampled" % sm_mhz,
+                     "traffic": traffic, "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+                     "peak_derivation": "2 FP64 ops/clk/SM (nominal 1.25 TFLOP/s) x 152 SMs x %.0f MHz sampled" % sm_mhz,
                      "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"), "peak_kind": peak_kind,
                              "frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0)}},
         "clocks": clocks,
