@@ -312,3 +312,28 @@ def test_beyond_2e31_elements_per_buffer(prec):
     f = s.get_f_region(n - 1, n - 1, 1, 1)[:, 0, 0].astype(np.float64)
     assert abs(rho[n - 1, n - 1] - f.sum()) <= 64 * np.finfo(np.float64).eps * np.abs(f).sum()
     s.close()
+
+
+def test_fp32_storage_density_is_the_correctly_rounded_exact_sum():
+    """FP32 storage sums a node's 33 values exactly (64-bit fixed point) and rounds once, so rho
+    read back equals the exact rational sum of the stored values, correctly rounded to FP64, bit
+    for bit. This holds unless a node has a term below 2^-55 of its largest one, which the test
+    checks and skips."""
+    from fractions import Fraction
+    w = W.riemann4q(n=96, seed=2, steps=30)
+    s = F.Solver.from_workload(w, F.FDLBM_FP32_STORE)
+    s.step(w.steps)
+    f = s.get_f()                      # (33, ny, nx), the stored FP32 values widened exactly
+    rho = s.get_macro()[0]
+    rng = np.random.default_rng(5)
+    checked = 0
+    for _ in range(300):
+        j, i = int(rng.integers(0, w.ny)), int(rng.integers(0, w.nx))
+        vals = f[:, j, i]
+        big = np.abs(vals).max()
+        if np.any((vals != 0) & (np.abs(vals) < big * 2.0 ** -55)):
+            continue
+        exact = sum(Fraction(float(v)) for v in vals)
+        assert rho[j, i] == float(exact), (j, i)
+        checked += 1
+    assert checked >= 250
