@@ -5,7 +5,8 @@
 A "step" is one time step of the whole method (moments -> f_eq -> Eq. 17 -> boundary fill) over
 the workload's grid. The metric is GLUPS: site updates of all 33 velocities per second (nx*ny*steps/s).
 
-Default workload: the 4096 x 4096 four-quadrant Riemann problem (FP32 f, FP64 moments and f_eq,
+Default workload: the 4096 x 4096 four-quadrant Riemann problem (FP32 f; moments summed exactly in
+fixed point and finished in FP64; FP64 f_eq;
 dx = 2.5e-4, dt = tau = 2.5e-6, lambda = 3, outflow on every side). Its f pair is 4.4 GB, far
 above the 129 MB L2, so no L2 flush is needed between steps.
 
@@ -400,7 +401,7 @@ def main():
         "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec_name == "fp64" else "f32-store/f64-moments-feq",
+        "dtype": "f64" if prec_name == "fp64" else "f32-store/fixed-point+f64-moments/f64-feq",
         "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "precision": prec_name,
                    "tile_variant": variant, "autotune_ms": [round(t, 4) for t in times],

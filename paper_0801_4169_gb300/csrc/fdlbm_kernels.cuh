@@ -4,20 +4,23 @@
 // and fdlbm_aux.cu (initial condition, boundary, moment and copy kernels).
 //
 // One fused kernel per time step computes, for every interior node of its tile:
-//   moments n, u, T, P of Eqs. 3-5            (FP64, tile + 1-node ring, staged in shared memory)
+//   moments n, u, T, P of Eqs. 3-5            (tile + 1-node ring, staged in shared memory; FP64
+//                                              sums, or exact fixed-point sums for FP32 storage)
 //   switch theta_alphaI (Eq. 16), kappa (Eq. 15)
 //   weights F_k(theta) (Eqs. 11-13) and f_eq (Eq. 10)        (FP64)
 //   Eq. 17 for all 33 velocities, both axes, relaxation once  (storage precision)
 // and writes f_new plus the ghost copies it owns (periodic wrap, zero-gradient copy, specular
 // mirror), so the next step needs no separate boundary pass.
 //
-// On this GPU an FP64 instruction (including an FP32<->FP64 conversion) issues at ~1.6/clk/SM,
-// ~73x below FP32, so the step is bound by the FP64 pipe, not by HBM. The code is arranged to
-// issue as few FP64 operations per node as the method allows:
-//   * ring moments from shared differences (S, X, Y per ring: 15 ops);
+// On this GPU an FP64 instruction (including an FP32<->FP64 conversion) issues at 2/clk/SM, ~64x
+// below FP32, so the step is bound by the FP64 pipe, not by HBM. The code is arranged to issue as
+// few FP64 operations per node as the method allows:
+//   * ring moments from shared differences (S, X, Y per ring: 15 ops with FP64 storage); with
+//     FP32 storage the ring sums are exact 64-bit integers and only the sqrt(1/2) and speed
+//     weights are applied in FP64;
 //   * f_eq by the even/odd split of each opposite-direction pair: with x = p^2,
 //       nF_k E = alpha + x (beta + gamma x),  nF_k O = p (delta + eps x),  f_eq(+-) = nF_k (E +- O),
-//     where (alpha..eps) are 5 per-ring constants (6 ops per pair);
+//     where (alpha..eps) are 5 per-ring constants (7 ops per ring, 4 per pair);
 //   * dt/tau folded into nF_k, so r*f_eq costs nothing extra;
 //   * the Eq. 17 weights of the +-1 neighbours combined with the node's viscosity once per
 //     (axis, |c| class, ring), shared by the 2-4 directions of that class.
