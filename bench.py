@@ -49,7 +49,11 @@ FP64_OPS_PER_LUP = {"fp64": 577, "fp32": 166}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this bench's 4096^2 workload
 # (single-pass capture), divided by the sites. Reported as roofline.traffic when the autotuner
 # picks the captured variant, else null.
-TRAFFIC_B_PER_SITE = {("fp32", 2): 264.1, ("fp64", 7): 842.8}
+TRAFFIC_B_PER_SITE = {("fp32", 2): 264.1, ("fp64", 7): 842.8, ("fp32", 11): 467.8, ("fp64", 10): 873.6}
+# Variants that split a step into two launches (moment pass + update pass). Their minimum bytes per
+# site update: f read twice and written once, the moment buffer (4 FP64 + P) written and read.
+SPLIT_VARIANTS = (10, 11)
+BYTES_PER_LUP_SPLIT = {"fp64": 3 * 33 * 8 + 2 * (4 * 8 + 8), "fp32": 3 * 33 * 4 + 2 * (4 * 8 + 4)}
 # Minimum HBM bytes per site update: read and write all 33 f once.
 BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4}
 # FP64 instructions (DADD + DFMA + DMUL) per amplification-matrix spectrum of the von Neumann
@@ -314,6 +318,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="a small version of the workload (profiling)")
     ap.add_argument("--n", type=int, default=None, help="grid edge of the four-quadrant workload (profiling)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="launch variant instead of the autotuner's choice (profiling: ncu's per-launch overhead "
+                         "biases the autotuner against two-launch variants)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -348,7 +355,11 @@ def main():
         t.numpy()[...] = a
         pinned.append(t.numpy())
     solver.set_macro(*pinned)
-    times = solver.autotune(3)
+    if args.variant is None:
+        times = solver.autotune(3)
+    else:
+        solver.set_variant(args.variant)
+        times = []
     variant = F.fdlbm_get_variant(solver.h)
     solver.step(args.warmup)
     solver.sync()
@@ -393,7 +404,8 @@ def main():
     fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * sm_mhz * 1e6 / 1e9  # G ops/s at the sampled clock
     site_rate = w.nx * w.ny / (per_launch_ms * 1e-3)
     achieved = FP64_OPS_PER_LUP[prec_name] * site_rate / 1e9
-    hbm_gbs = BYTES_PER_LUP[prec_name] * site_rate / 1e9
+    split = variant in SPLIT_VARIANTS
+    hbm_gbs = (BYTES_PER_LUP_SPLIT if split else BYTES_PER_LUP)[prec_name] * site_rate / 1e9
     tb = TRAFFIC_B_PER_SITE.get((prec_name, variant)) if (w.nx, w.ny) == (4096, 4096) else None
     traffic = tb * w.nx * w.ny if tb else None
 
@@ -408,9 +420,10 @@ def main():
                    "l2": "inputs larger than L2 (f pair %.2f GB)" % (2 * 33 * w.nx * w.ny * (8 if prec_name == "fp64" else 4) / 1e9)
                    if w.nx * w.ny * 33 * 4 > 129e6 else "inputs smaller than L2: steps read a warm cache",
                    "status": status, "parallelism": "replicas%d" % world},
-        "roofline": {"bound": "alu", "kernel": "k_step (fused step)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_moments + k_update (split step)" if split else "k_step (fused step)",
+                     "achieved": achieved,
                      "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak,
-                     "traffic": traffic, "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+                     "traffic": traffic, "traffic_unit": "bytes per step (ncu DRAM read + write of its launches)",
                      "peak_derivation": "2 FP64 ops/clk/SM (nominal 1.25 TFLOP/s) x 152 SMs x %.0f MHz sampled" % sm_mhz,
                      "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"), "peak_kind": peak_kind,
                              "frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0)}},
@@ -418,7 +431,7 @@ def main():
         "e2e": {"value": e2e_glups, "unit": "GLUPS", "h2d_bytes_per_step": macro_bytes / args.steps,
                 "d2h_bytes_per_step": macro_bytes / args.steps, "status": int(rc),
                 "note": "one solve per timed region: set_macro (H2D) + %d steps + get_macro (D2H)" % args.steps},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if split else 1),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.workload, budget_s=20.0)

@@ -76,7 +76,11 @@ Layout layout_of(const fdlbm_config* c) {
   L.fbytes = round_up((size_t)Q * L.g.plane * L.esize, 256);
   L.health_off = 2 * L.fbytes;
   L.stage_off = L.health_off + 256;
-  L.total = L.stage_off + round_up((size_t)4 * c->nx * c->ny * sizeof(double), 256);
+  L.mom_off = L.stage_off + round_up((size_t)4 * c->nx * c->ny * sizeof(double), 256);
+  // moment buffer of the split step: 4 FP64 planes + P in the storage precision
+  L.mom_bytes = (long long)c->nx * c->ny > 65536 ? round_up((size_t)L.g.plane * (4 * sizeof(double) + L.esize), 256) : 0;
+  L.total = L.mom_off + L.mom_bytes;
+  L.g.mom = nullptr;  // set to the handle's buffer once its memory is known
   return L;
 }
 
@@ -284,6 +288,7 @@ int fdlbm_create_ex(fdlbm_t* out, const fdlbm_config* cfg, void* device_mem, siz
   h->f[1] = h->mem + L.fbytes;
   h->d_health = reinterpret_cast<unsigned*>(h->mem + L.health_off);
   h->d_stage = reinterpret_cast<double*>(h->mem + L.stage_off);
+  h->grid.mom = L.mom_bytes ? static_cast<void*>(h->mem + L.mom_off) : nullptr;
   e = cudaMallocHost(&h->h_health, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->mem, 0, 2 * L.fbytes + 256, h->stream);
@@ -583,6 +588,8 @@ int fdlbm_variant_count(void) { return V_COUNT; }
 int fdlbm_set_variant(fdlbm_t h, int variant) {
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (variant < 0 || variant >= V_COUNT) return fail(h, FDLBM_E_ARG, "variant out of range");
+  if (variant_needs_mom(variant) && !h->grid.mom)
+    return fail(h, FDLBM_E_ARG, "the split variants need a moment buffer, which grids of up to 65536 sites do not have");
   h->variant = variant;
   return FDLBM_OK;
 }
@@ -604,6 +611,10 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
   int best = h->variant;
   float best_ms = 1e30f;
   for (int v = 0; v < V_COUNT && e == cudaSuccess; ++v) {
+    if (variant_needs_mom(v) && !h->grid.mom) {  // not available on this grid
+      if (times_ms) times_ms[v] = 0.f;
+      continue;
+    }
     // warm-up launch, then the timed ones; every launch maps f[cur] -> f[1-cur]
     e = launch_step(h->cfg.prec, v, h->f[h->cur], h->f[1 - h->cur], h->grid, h->coeffs, h->d_health, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);

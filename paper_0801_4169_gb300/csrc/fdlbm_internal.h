@@ -37,6 +37,9 @@ struct Grid {
   long long plane;  // pitch * rows (elements per velocity plane)
   int bc[4];        // left, right, bottom, top
   int flags;
+  // Moment buffer of the split step (V_S* variants), or null: planes n, ux, uy, T (FP64) and P
+  // (storage precision) over the padded grid, indexed like f. Only grids above 65 536 sites have one.
+  void* mom;
 };
 
 // Per-solve constants computed once on the host in FP64 and passed by value (kernel parameter
@@ -89,10 +92,14 @@ inline void variant_tile(int v, int* tw, int* th) {
 // the precision and the grid, and the autotuner measures it.
 // V_RP* are the ring-parallel variants (four lanes per node) for small grids; batches use the
 // tile variants only (V_TILE_COUNT).
+// V_S* split the step in two launches: k_moments writes every node's moments once to the grid's
+// moment buffer, and the update pass stages them for its tile and ring instead of recomputing
+// them. Same functions, so the results are bitwise those of the fused variants.
 enum StepVariant {
   V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_T32x32 = 5, V_T32x24 = 6,
-  V_T32x28 = 7, V_TILE_COUNT = 8, V_RP16x4 = 8, V_RP8x4 = 9, V_COUNT = 10
+  V_T32x28 = 7, V_TILE_COUNT = 8, V_RP16x4 = 8, V_RP8x4 = 9, V_S32x16 = 10, V_S32x32 = 11, V_COUNT = 12
 };
+inline bool variant_needs_mom(int v) { return v == V_S32x16 || v == V_S32x32; }
 
 // Kernel launchers (fdlbm_aux.cu, fdlbm_step_f32.cu, fdlbm_step_f64.cu). All return
 // cudaGetLastError() of the launch.
@@ -121,7 +128,7 @@ cudaError_t launch_set_f(int prec, void* f, const Grid& g, const double* in, cud
 // Host helpers shared by the C ABI files (fdlbm_capi.cu).
 struct Layout {
   Grid g;
-  size_t esize, fbytes, health_off, stage_off, total;
+  size_t esize, fbytes, health_off, stage_off, mom_off, mom_bytes, total;
 };
 bool valid_cfg(const fdlbm_config* c, std::string* why);
 Layout layout_of(const fdlbm_config* c);

@@ -621,7 +621,41 @@ __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 // n, ux, uy, T, P of the tile and its 1-node ring (corners excluded), computed once per node.
 // One tile (tx, ty) of one solve: the body shared by the single-solve kernel (k_step) and the
 // batched kernel (k_step_batch), so a node's arithmetic is the same alone and in a batch.
-template <typename S, int BX, int BY, int RY>
+// Moment buffer planes (split step): n, ux, uy, T in FP64, then P in the storage precision.
+template <typename S>
+struct MomPlanes {
+  double *n, *ux, *uy, *T;
+  S* P;
+};
+template <typename S>
+__device__ __forceinline__ MomPlanes<S> mom_planes(const Grid& g) {
+  double* b = static_cast<double*>(g.mom);
+  return MomPlanes<S>{b, b + g.plane, b + 2 * g.plane, b + 3 * g.plane, reinterpret_cast<S*>(b + 4 * g.plane)};
+}
+// a node of the tile ring is needed unless it is a corner of the padded region
+__device__ __forceinline__ bool ring_node_needed(const Grid& g, int gx, int gy) {
+  const bool inx = gx >= 0 && gx < g.nx, iny = gy >= 0 && gy < g.ny;
+  return (inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny));
+}
+
+// Split step, pass 1: the moments of every interior node and of the ghost layer next to each edge,
+// once, into the moment buffer (with the NUMERIC health check).
+template <typename S>
+__global__ void k_moments(const S* __restrict__ f, Grid g, Coeffs c, unsigned* __restrict__ health) {
+  const int gx = blockIdx.x * blockDim.x + threadIdx.x - 1, gy = blockIdx.y * blockDim.y + threadIdx.y - 1;
+  if (gx > g.nx || gy > g.ny || !ring_node_needed(g, gx, gy)) return;
+  const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
+  const Macro m = to_macro(node_moments(f, g.plane, off, c));
+  if (!macro_ok(m)) atomicOr(health, H_NUMERIC);
+  const MomPlanes<S> M = mom_planes<S>(g);
+  M.n[off] = m.n;
+  M.ux[off] = m.ux;
+  M.uy[off] = m.uy;
+  M.T[off] = m.T;
+  M.P[off] = from_d<S>(m.P);
+}
+
+template <typename S, int BX, int BY, int RY, bool FROM_BUF = false>
 __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict__ fn, const Grid& g, const Coeffs& c,
                                           unsigned* __restrict__ health, int tx, int ty) {
   constexpr int TW = BX, TH = BY * RY, SW = TW + 2, SH = TH + 2, NT = BX * BY;
@@ -637,8 +671,23 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
   // Phase 1: moments on the tile and its ring (needed: interior nodes and the ghost layer next
   // to an edge, never the corners). Branch-free and unrolled over a thread's slots, so the FP64
   // chains of its 2-3 nodes interleave: every slot loads from an address clamped into the padded
-  // grid, and only needed nodes are stored and health-checked.
+  // grid, and only needed nodes are stored and health-checked. The split step reads them from
+  // the moment buffer instead.
   constexpr int NSLOT = (SW * SH + NT - 1) / NT;
+  if constexpr (FROM_BUF) {
+    const MomPlanes<S> M = mom_planes<S>(g);
+    for (int idx = tid; idx < SW * SH; idx += NT) {
+      const int lx = idx % SW, ly = idx / SW;
+      const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+      if (gx > g.nx || gy > g.ny || !ring_node_needed(g, gx, gy)) continue;
+      const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
+      s_n[ly][lx] = M.n[off];
+      s_ux[ly][lx] = M.ux[off];
+      s_uy[ly][lx] = M.uy[off];
+      s_T[ly][lx] = M.T[off];
+      s_P[ly][lx] = M.P[off];
+    }
+  } else {
 #pragma unroll
   for (int k = 0; k < NSLOT; ++k) {
     const int idx = tid + k * NT;
@@ -659,6 +708,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       s_T[ly][lx] = m.T;
       s_P[ly][lx] = from_d<S>(m.P);
     }
+  }
   }
   __syncthreads();
 
@@ -712,6 +762,12 @@ template <typename S, int BX, int BY, int RY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f, S* __restrict__ fn, Grid g, Coeffs c,
                                                   unsigned* __restrict__ health) {
   step_tile<S, BX, BY, RY>(f, fn, g, c, health, blockIdx.x, blockIdx.y);
+}
+// Split step, pass 2: the update with the tile's moments read from the moment buffer.
+template <typename S, int BX, int BY, int RY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB) k_update(const S* __restrict__ f, S* __restrict__ fn, Grid g,
+                                                    Coeffs c, unsigned* __restrict__ health) {
+  step_tile<S, BX, BY, RY, true>(f, fn, g, c, health, blockIdx.x, blockIdx.y);
 }
 
 // Batched step: every member solve of a batch advances one time step in one launch. Members share
@@ -1008,10 +1064,23 @@ cudaError_t launch_rp_t(const void* f, void* fn, const Grid& g, const Coeffs& c,
   return cudaGetLastError();
 }
 
+template <typename S, int BX, int BY, int RY, int MINB>
+cudaError_t launch_split_t(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health, cudaStream_t s) {
+  if (!g.mom) return cudaErrorInvalidValue;
+  dim3 mb(32, 8), mg((g.nx + 2 + 31) / 32, (g.ny + 2 + 7) / 8);
+  k_moments<S><<<mg, mb, 0, s>>>(static_cast<const S*>(f), g, c, health);
+  dim3 block(BX, BY);
+  dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY * RY - 1) / (BY * RY));
+  k_update<S, BX, BY, RY, MINB><<<grid, block, 0, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g, c, health);
+  return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_step_v(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
   switch (variant) {
+    case V_S32x16: return launch_split_t<S, 32, 8, 2, 2>(f, fn, g, c, health, s);
+    case V_S32x32: return launch_split_t<S, 32, 8, 4, 2>(f, fn, g, c, health, s);
     case V_RP16x4: return launch_rp_t<S, 16, 4>(f, fn, g, c, health, s);
     case V_RP8x4: return launch_rp_t<S, 8, 4>(f, fn, g, c, health, s);
     case V_T32x4: return launch_step_t<S, 32, 4, 1, 4>(f, fn, g, c, health, s);

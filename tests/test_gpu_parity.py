@@ -112,9 +112,14 @@ def test_scheme_variants_match_oracle(flags):
     assert np.max(np.abs(fg - fo)) <= 1e-12 * np.abs(fo).max()
 
 
+SPLIT_VARIANTS = (10, 11)  # two launches per step, moments through the moment buffer
+
+
 def test_variants_are_bitwise_identical():
-    """A node's arithmetic does not depend on the tile shape: all variants agree bit for bit."""
-    cases = [(W.riemann4q(n=160, steps=40), F.FDLBM_FP32_STORE), (W.reflection(nx=300, ny=75, steps=40), F.FDLBM_FP64)]
+    """A node's arithmetic does not depend on the tile shape or on the step being split in two
+    launches: all variants agree bit for bit. The grids exceed 65 536 sites, so they have the
+    moment buffer the split variants need."""
+    cases = [(W.riemann4q(n=272, steps=40), F.FDLBM_FP32_STORE), (W.reflection(nx=600, ny=150, steps=40), F.FDLBM_FP64)]
     for w, prec in cases:
         ref = None
         for v in range(F.fdlbm_variant_count()):
@@ -220,13 +225,47 @@ def test_device_pointer_calls_and_caller_stream():
 
 
 def test_autotune_keeps_state():
-    w = W.riemann4q(n=200, steps=10)
+    w = W.riemann4q(n=272, steps=10)
     s = F.Solver.from_workload(w, F.FDLBM_FP32_STORE)
     f0 = s.get_f()
     times = s.autotune(3)
     assert len(times) == F.fdlbm_variant_count() and all(t > 0 for t in times)
     assert np.array_equal(s.get_f(), f0)
     assert s.steps_done == 0
+
+
+def test_split_variants_need_a_moment_buffer():
+    """Grids of up to 65 536 sites have no moment buffer: the split variants are refused and the
+    autotuner reports them as not timed (0)."""
+    w = W.riemann4q(n=200, steps=10)
+    s = F.Solver.from_workload(w, F.FDLBM_FP32_STORE)
+    for v in SPLIT_VARIANTS:
+        with pytest.raises(F.FdlbmError) as ei:
+            s.set_variant(v)
+        assert ei.value.code == F.FDLBM_E_ARG
+    times = s.autotune(2)
+    assert all(times[v] == 0 for v in SPLIT_VARIANTS) and all(t > 0 for v, t in enumerate(times) if v not in SPLIT_VARIANTS)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 3, 2), (2, 3, 1, 3)])
+def test_split_step_matches_oracle_all_boundaries(bc):
+    """The split step (moments pass + update pass) on a ragged 301 x 230 grid, every boundary kind:
+    the moment pass covers the ghost layer next to each edge."""
+    nx, ny, steps = 301, 230, 6
+    bstate = np.zeros((4, 4))
+    for side in range(4):
+        bstate[side] = (1.1 + 0.1 * side, 0.2, -0.1, 0.9)
+    fields = _smooth(nx, ny, 7)
+    s = F.Solver(nx, ny, 1e-3, 1.2e-3, 1e-5, 1.5e-5, 1.5, bc, F.FDLBM_FP64, 0, bstate)
+    s.set_variant(SPLIT_VARIANTS[0])
+    s.set_macro(*fields)
+    s.step(steps)
+    fg = s.get_f()
+    o = O.Sim(nx, ny, 1e-3, 1.2e-3, 1e-5, 1.5e-5, 1.5, bc, bstate)
+    o.set_macro(*fields)
+    assert o.step(steps) == 0
+    fo = o.get_f()
+    assert np.max(np.abs(fg - fo)) <= 1e-12 * np.abs(fo).max()
 
 
 def _window_update(win, w):
