@@ -252,16 +252,20 @@ __device__ __forceinline__ Mom node_moments(const double* __restrict__ f, long l
   return combine_rings(ld(f + off), S, X, Y, c);
 }
 
-// FP32 storage: the moments are summed exactly in 64-bit fixed point on the integer pipe, which
+// FP32 storage: the moments are summed exactly in 64-bit fixed point on the integer pipes, which
 // replaces ~55 of the ~80 FP64 operations of the FP64 summation.
 //  - Scale: with e* the largest biased exponent of the node's 33 values (subnormals count as 1), a
-//    value x becomes the integer trunc(x 2^(181 - e*)): its 24-bit significand shifted so that the
-//    largest value's top bit lands on bit 54. A value below 2^-55 of the largest loses the bits
-//    under the unit; the error is below 2^-54 of the largest value per term, less than one
-//    rounding of an FP64 sum. Any sum of 33 terms stays below 2^61.
-//  - Per ring, the integers S = sum g, AX = g7 - g3, DX = (g0 - g4) + (g6 - g2), AY = g1 - g5,
-//    DY = (g0 - g4) - (g6 - g2) are exact, as is N = f_0 + sum_k S_k. They are converted to FP64 by
-//    integer bit operations with one rounding each (fix_to_f64). In FP64:
+//    value x = +-m 2^(e-150) (m its 24-bit significand) enters as the integer +-m 2^(30-e*+e): the
+//    largest value's top bit lands on bit 53. A term more than 2^30 below the largest has its
+//    significand shifted right (arithmetic shift, rounding towards -inf) and loses the bits under
+//    the unit, less than 2^-53 of the largest value per term, below one rounding of an FP64 sum.
+//    Any sum of 33 terms stays below 2^60.
+//  - Each term is one 32 x 32 -> 64-bit multiply-add of the signed significand by a power of two,
+//    accumulated straight into the ring sums (the multiply-add runs on the FMA pipe, which the
+//    step leaves idle, instead of the shifts and 64-bit adds of the integer ALU):
+//    S = sum g, AX = g7 - g3, DX = (g0 - g4) + (g6 - g2), AY = g1 - g5, DY = (g0 - g4) - (g6 - g2),
+//    and N = f_0 + sum_k S_k, all exact. They are converted to FP64 by integer bit operations with
+//    one rounding each (fix_to_f64). In FP64:
 //      n = N,  X_k = fma(s, DX_k, AX_k),  Y_k = fma(s, DY_k, AY_k),
 //    and jx, jy, sum |v|^2 f follow the pairwise ring tree of combine_rings.
 //  - Integer sums are associative, so the ring-parallel kernel, which adds its lanes' integers in
@@ -272,13 +276,24 @@ __device__ __forceinline__ int f32_exp1(float x) {
   const int e = (int)((__float_as_uint(x) >> 23) & 0xffu);
   return e ? e : 1;
 }
-__device__ __forceinline__ long long to_fix(float x, int emax) {
+// The term of x as (significand, power of two): x enters the sums as (long long)sm * p.
+struct FixTerm {
+  int sm, p;
+};
+__device__ __forceinline__ FixTerm fix_term(float x, int emax) {
   const unsigned u = __float_as_uint(x);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
-  const int sh = emax - (e ? (int)e : 1);  // 0 .. 253 for finite values
-  const unsigned long long t = sh < 64 ? (((unsigned long long)m << 31) >> sh) : 0ull;
-  return (u >> 31) ? -(long long)t : (long long)t;
+  const int e = (int)((u >> 23) & 0xffu);
+  const int m = (int)((u & 0x7fffffu) | (e ? 0x800000u : 0u));
+  const int sm = (int)(u >> 31) ? -m : m;
+  const int k = 30 - (emax - (e ? e : 1));  // <= 30
+  FixTerm t;
+  t.sm = k >= 0 ? sm : (sm >> min(-k, 31));
+  t.p = k >= 0 ? (1 << k) : 1;
+  return t;
+}
+__device__ __forceinline__ long long to_fix(float x, int emax) {
+  const FixTerm t = fix_term(x, emax);
+  return (long long)t.sm * t.p;
 }
 // V * 2^e2, rounded to nearest even, built from the integer's bits (|V| < 2^62, normal result).
 __device__ __forceinline__ double fix_to_f64(long long V, int e2) {
@@ -299,15 +314,18 @@ struct RingFix {
   long long S, AX, DX, AY, DY;
 };
 __device__ __forceinline__ RingFix ring_fix(const float (&x)[8], int emax) {
-  long long g[8];
+  FixTerm t[8];
 #pragma unroll
-  for (int d = 0; d < 8; ++d) g[d] = to_fix(x[d], emax);
+  for (int d = 0; d < 8; ++d) t[d] = fix_term(x[d], emax);
   RingFix r;
-  r.S = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]));
-  const long long a = g[0] - g[4], b = g[6] - g[2];
-  r.AX = g[7] - g[3];
+  r.S = 0;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) r.S += (long long)t[d].sm * t[d].p;
+  r.AX = (long long)t[7].sm * t[7].p - (long long)t[3].sm * t[3].p;
+  r.AY = (long long)t[1].sm * t[1].p - (long long)t[5].sm * t[5].p;
+  const long long a = (long long)t[0].sm * t[0].p - (long long)t[4].sm * t[4].p;
+  const long long b = (long long)t[6].sm * t[6].p - (long long)t[2].sm * t[2].p;
   r.DX = a + b;
-  r.AY = g[1] - g[5];
   r.DY = a - b;
   return r;
 }
@@ -331,7 +349,7 @@ __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long lo
     emax = max(emax, f32_exp1(x[q]));
   }
   if (emax == 255) return nan_moments();
-  const int e2 = emax - 181;
+  const int e2 = emax - 180;
   long long N = to_fix(x[0], emax);
   double S[4], X[4], Y[4];
 #pragma unroll
@@ -386,7 +404,7 @@ __device__ __forceinline__ void quad_ring(const float* __restrict__ f, long long
   long long N = rf.S + (r == 0 ? to_fix(x0, emax) : 0ll);
   N += __shfl_xor_sync(0xffffffffu, N, 1);
   N += __shfl_xor_sync(0xffffffffu, N, 2);
-  const int e2 = emax - 181;
+  const int e2 = emax - 180;
   ring_from_fix(rf, e2, S, X, Y);
   n = fix_to_f64(N, e2);
   if (emax == 255) {
