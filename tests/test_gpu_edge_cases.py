@@ -1,0 +1,125 @@
+"""Degenerate inputs and states on the GPU: zero steps, empty batches, one-node grids, uniform and
+y-uniform states, |kappa| > 1, non-positive density. Each is checked against what the scheme or
+the oracle fixes."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import fdlbm as O  # noqa: E402
+from paper_0801_4169_gb300 import fdlbm as F  # noqa: E402
+from paper_0801_4169_gb300 import workloads as W  # noqa: E402
+
+PER = (0, 0, 0, 0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    F.lib()
+
+
+def _uniform(nx, ny, state):
+    return [np.full((ny, nx), float(c)) for c in state]
+
+
+def test_zero_steps_and_empty_batches_are_no_ops():
+    w = W.sod(nx=64, ny=4)
+    s = F.Solver.from_workload(w, F.FDLBM_FP64)
+    f0 = s.get_f()
+    s.step(0)
+    assert s.sync() == 0 and s.steps_done == 0 and np.array_equal(s.get_f(), f0)
+    b = F.fdlbm_batch_create()
+    F.fdlbm_batch_step(b, 5)                      # no members: nothing to do
+    failed, words = F.fdlbm_batch_sync(b)
+    assert failed == 0 and len(words) == 0
+    F.fdlbm_batch_add(b, s.h)
+    F.fdlbm_batch_step(b, 0)
+    F.fdlbm_batch_sync(b)
+    assert s.steps_done == 0 and np.array_equal(s.get_f(), f0)
+    F.fdlbm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", [F.FDLBM_FP64, F.FDLBM_FP32_STORE])
+def test_uniform_state_is_a_fixed_point(prec):
+    """A uniform equilibrium on a periodic grid: every difference in Eq. 17 vanishes, and f_eq of
+    the moments of f_eq is f_eq up to rounding. After 200 steps every velocity plane is still
+    constant (bit for bit) and within rounding of the start."""
+    nx, ny = 48, 40
+    s = F.Solver(nx, ny, 1e-3, 1e-3, 1e-5, 2e-5, 1.0, PER, prec)
+    s.set_macro(*_uniform(nx, ny, (1.3, 0.4, -0.2, 0.7)))
+    f0 = s.get_f()
+    s.step(200)
+    f = s.get_f()
+    assert s.sync() == 0
+    for q in range(33):
+        assert np.all(f[q] == f[q, 0, 0]), q
+    eps = np.finfo(np.float64 if prec == F.FDLBM_FP64 else np.float32).eps
+    assert np.max(np.abs(f - f0)) <= 200 * 64 * eps * np.abs(f0).sum(axis=0).max()
+
+
+def test_y_uniform_data_stays_y_uniform_bit_for_bit():
+    """Rows that start identical on a y-periodic grid stay identical: the y-differences are exact
+    zeros and every row computes the same arithmetic, in every launch variant."""
+    w = W.shock_tube(nx=300, ny=8, Ms=4.0, U=2.0)
+    for v in range(F.fdlbm_variant_count()):
+        s = F.Solver.from_workload(w, F.FDLBM_FP64)
+        try:
+            s.set_variant(v)
+        except F.FdlbmError:
+            continue  # split variants need grids above 65 536 sites
+        s.step(150)
+        f = s.get_f()
+        assert s.sync() == 0
+        assert np.all(f == f[:, :1, :]), v
+
+
+def test_one_node_grid():
+    """nx = ny = 1, periodic: the node is its own neighbour in both directions, the differences
+    vanish, and the state relaxes to itself like the oracle's."""
+    s = F.Solver(1, 1, 1e-3, 1e-3, 1e-5, 1e-5, 1.0, PER, F.FDLBM_FP64)
+    fields = _uniform(1, 1, (1.1, 0.3, 0.2, 0.9))
+    s.set_macro(*fields)
+    s.step(25)
+    o = O.Sim(1, 1, 1e-3, 1e-3, 1e-5, 1e-5, 1.0, PER)
+    o.set_macro(*fields)
+    assert o.step(25) == 0
+    assert np.max(np.abs(s.get_f() - o.get_f())) <= 1e-14 * np.abs(o.get_f()).max()
+
+
+def test_kappa_above_one_is_flagged_not_clamped():
+    """|kappa| = |u| dt/dx > 1 is reported in the health word and not clamped (the scheme is used
+    as printed): one step still matches the oracle, which applies the same (1 - |kappa|) factor, to
+    the one-step bound 512 eps kappa_c max|f| (kappa_c = sum|f_eq|/n, the conditioning)."""
+    nx, ny, dx, dt = 16, 4, 1e-3, 5e-4
+    fields = _uniform(nx, ny, (1.0, 0.0, 0.0, 1.0))
+    fields[1][:, :8] = 3.0  # u dt/dx = 1.5 on half the grid, at a well-conditioned state
+    s = F.Solver(nx, ny, dx, dx, dt, dt, 0.5, PER, F.FDLBM_FP64)
+    s.set_macro(*fields)
+    s.step(1)
+    assert F.fdlbm_health(s.h) & F.FDLBM_HEALTH_KAPPA
+    o = O.Sim(nx, ny, dx, dx, dt, dt, 0.5, PER)
+    o.set_macro(*fields)
+    assert o.step(1) == 0
+    fe = O.feq(1.0, 3.0, 0.0, 1.0)
+    kappa_c = np.abs(fe).sum() / fe.sum()
+    ref = o.get_f()
+    assert np.max(np.abs(s.get_f() - ref)) <= 512 * np.finfo(float).eps * kappa_c * np.abs(ref).max()
+
+
+def test_nonpositive_density_is_a_numerical_failure_like_the_oracle():
+    nx, ny = 12, 4
+    fields = _uniform(nx, ny, (1.0, 0.1, 0.0, 1.0))
+    fields[0][1, 5] = -0.5
+    s = F.Solver(nx, ny, 1e-3, 1e-3, 1e-5, 1e-5, 1.0, PER, F.FDLBM_FP64)
+    s.set_macro(*fields)
+    s.step(1)
+    with pytest.raises(F.FdlbmError) as ei:
+        s.sync()
+    assert ei.value.code == F.FDLBM_E_NUMERIC
+    o = O.Sim(nx, ny, 1e-3, 1e-3, 1e-5, 1e-5, 1.0, PER)
+    o.set_macro(*fields)
+    assert o.step(1) == -4
