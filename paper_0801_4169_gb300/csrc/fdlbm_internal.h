@@ -17,8 +17,11 @@ namespace fdlbm {
 constexpr int Q = 33;   // Watari-Tsutahara velocity count: rest + 4 speeds x 8 directions (Eq. 1)
 constexpr int NG = 2;   // ghost ring width: Eq. 17 reaches I +- 2 along each axis
 
-// Speeds v_1..v_4 of the four rings (the values of Sec. 4, used for every problem).
-__host__ __device__ constexpr double speed(int k) { return k == 0 ? 1.0 : k == 1 ? 1.92 : k == 2 ? 2.99 : 4.49; }
+// Speeds v_1..v_4 of the four rings (the values of Sec. 4, used for every problem). They have two
+// decimals, so 100 v_k is an integer (the fixed-point moment sums weight by it exactly); v_k is
+// that integer over 100, correctly rounded, which is the FP64 value of the decimal.
+__host__ __device__ constexpr int speed_c(int k) { return k == 0 ? 100 : k == 1 ? 192 : k == 2 ? 299 : 449; }
+__host__ __device__ constexpr double speed(int k) { return speed_c(k) / 100.0; }
 
 // Scheme flags (same values as enum fdlbm_flags).
 constexpr int F_NO_LW = 1, F_NO_DISP = 2, F_NO_VISC = 4, F_SWITCH_CONST = 8;

@@ -16,8 +16,8 @@
 // below FP32, so the step is bound by the FP64 pipe, not by HBM. The code is arranged to issue as
 // few FP64 operations per node as the method allows:
 //   * ring moments from shared differences (S, X, Y per ring: 15 ops with FP64 storage); with
-//     FP32 storage the ring sums are exact 64-bit integers and only the sqrt(1/2) and speed
-//     weights are applied in FP64;
+//     FP32 storage the ring sums and the speed-weighted momentum sums are exact 64-bit integers,
+//     and only sqrt(1/2), the energy's v_k^2 and 1/100 are applied in FP64;
 //   * f_eq by the even/odd split of each opposite-direction pair: with x = p^2,
 //       nF_k E = alpha + x (beta + gamma x),  nF_k O = p (delta + eps x),  f_eq(+-) = nF_k (E +- O),
 //     where (alpha..eps) are 5 per-ring constants (7 ops per ring, 4 per pair);
@@ -37,28 +37,44 @@ __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }
 
-// FP32 <-> FP64 conversions issue on the (slow) FP64 pipe. For normal numbers both directions
-// are done bit-exactly with integer operations instead; zero, subnormal, inf/nan and values
-// outside the FP32 normal range take the hardware conversion.
-//   up:   exponent += 1023 - 127, mantissa shifted left by 29 (exact).
-//   down: round to nearest even on the 29 dropped mantissa bits (a carry into the exponent is
-//         the correct rounding, up to +inf).
-__device__ __forceinline__ bool f32_special(float x) {
-  const unsigned a = __float_as_uint(x) & 0x7fffffffu;
-  return a - 0x00800000u >= 0x7f000000u;  // a < 2^-126 (zero/subnormal) or inf/nan
-}
+// FP32 <-> FP64 conversions issue on the (slow) FP64 pipe, so both directions are done bit-exactly
+// with integer operations instead, from the IEEE-754 formats:
+//   up (normal FP32 values only): exponent += 1023 - 127, significand shifted left by 29 (exact).
+//   down: round to nearest even on the 29 dropped significand bits (a carry into the exponent is
+//         the correct rounding, up to +inf). Values below 2^-126 round to the subnormal grid
+//         2^-149, values from 2^128 up become inf, and NaN stays NaN.
+// The rare cases are integer code in a function that is not inlined, behind a branch: a hardware
+// conversion, or an inlined rare path, under a predicate would still issue with every call.
 __device__ __forceinline__ double f32_to_f64_bits(float x) {
   const unsigned u = __float_as_uint(x);
   const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
   return __hiloint2double((int)hi, (int)(u << 29));
 }
+// |x| in [2^-126, 2^128) from its FP64 bits without the sign (ah: high word, lo: low word)
+__device__ __forceinline__ unsigned f64_to_f32_normal(unsigned ah, unsigned lo) {
+  const unsigned t = ((ah - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  return t + ((rem > 0x10000000u) | ((rem == 0x10000000u) & (t & 1u)));
+}
+// |x| outside [2^-126, 2^128): NaN, inf, or an FP32 subnormal or zero
+__device__ __noinline__ unsigned f64_to_f32_rare(unsigned ah, unsigned lo) {
+  if (ah >= 0x7ff00000u) return (ah > 0x7ff00000u || lo != 0u) ? 0x7fc00000u : 0x7f800000u;
+  if (ah >= (1151u << 20)) return 0x7f800000u;
+  // below 2^-126: the significand m has unit 2^(E-1075) (E the biased exponent, 1 for FP64
+  // subnormals) and the result unit 2^-149, so the result is m 2^-sh rounded, sh = 926 - E >= 30
+  const unsigned E = ah >> 20;
+  const unsigned sh = 926u - (E ? E : 1u);
+  if (sh >= 64u) return 0u;  // m < 2^53: below half the result unit
+  const unsigned long long m = ((unsigned long long)((ah & 0xfffffu) | (E ? 0x100000u : 0u)) << 32) | lo;
+  const unsigned long long q = m >> sh, r = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);
+  return (unsigned)q + (unsigned)((r > half) | ((r == half) & (q & 1ull)));  // a carry gives 2^-126
+}
 __device__ __forceinline__ float f64_to_f32_rn(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const unsigned ah = hi & 0x7fffffffu;
-  if (ah - (897u << 20) >= (254u << 20)) return __double2float_rn(x);  // not an FP32 normal
-  unsigned t = ((ah - (896u << 20)) << 3) | (lo >> 29);
-  const unsigned rem = lo & 0x1fffffffu;
-  t += (rem > 0x10000000u) | ((rem == 0x10000000u) & (t & 1u));
+  unsigned t;
+  if (__builtin_expect(ah - (897u << 20) < (254u << 20), 1)) t = f64_to_f32_normal(ah, lo);
+  else t = f64_to_f32_rare(ah, lo);
   return __uint_as_float(t | (hi & 0x80000000u));
 }
 
@@ -66,9 +82,10 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
 // third-order Newton step y (1 + e + e^2), e = 1 - x y, leaving O(e^3) ~ 2^-69: full FP64
 // accuracy up to the last-bit rounding, in 3 FMAs. Outside that range: IEEE division.
 __device__ __forceinline__ double rcp64(double x) {
-  const unsigned ah = (unsigned)__double2hiint(x) & 0x7fffffffu;
+  const unsigned hi = (unsigned)__double2hiint(x), ah = hi & 0x7fffffffu;
   if (ah - (897u << 20) >= (252u << 20)) return 1.0 / x;
-  const double y = f32_to_f64_bits(__frcp_rn(f64_to_f32_rn(x)));
+  const float xs = __uint_as_float(f64_to_f32_normal(ah, (unsigned)__double2loint(x)) | (hi & 0x80000000u));
+  const double y = f32_to_f64_bits(__frcp_rn(xs));
   const double e = fma(-x, y, 1.0);
   return fma(y, fma(e, e, e), y);
 }
@@ -253,21 +270,25 @@ __device__ __forceinline__ Mom node_moments(const double* __restrict__ f, long l
 }
 
 // FP32 storage: the moments are summed exactly in 64-bit fixed point on the integer pipes, which
-// replaces ~55 of the ~80 FP64 operations of the FP64 summation.
+// replaces ~70 of the ~80 FP64 operations of the FP64 summation.
 //  - Scale: with e* the largest biased exponent of the node's 33 values (subnormals count as 1), a
-//    value x = +-m 2^(e-150) (m its 24-bit significand) enters as the integer +-m 2^(30-e*+e): the
-//    largest value's top bit lands on bit 53. A term more than 2^30 below the largest has its
+//    value x = +-m 2^(e-150) (m its 24-bit significand) enters as the integer +-m 2^(26-e*+e): the
+//    largest value's top bit lands on bit 49. A term more than 2^26 below the largest has its
 //    significand shifted right (arithmetic shift, rounding towards -inf) and loses the bits under
-//    the unit, less than 2^-53 of the largest value per term, below one rounding of an FP64 sum.
-//    Any sum of 33 terms stays below 2^60.
+//    the unit, less than 2^-49 of the largest value per term (the FP32 values themselves carry
+//    2^-24). Every sum below stays under 2^63 (the speed-weighted ones under 1040 * 4 * 2^50).
 //  - Each term is one 32 x 32 -> 64-bit multiply-add of the signed significand by a power of two,
 //    accumulated straight into the ring sums (the multiply-add runs on the FMA pipe, which the
 //    step leaves idle, instead of the shifts and 64-bit adds of the integer ALU):
-//    S = sum g, AX = g7 - g3, DX = (g0 - g4) + (g6 - g2), AY = g1 - g5, DY = (g0 - g4) - (g6 - g2),
-//    and N = f_0 + sum_k S_k, all exact. They are converted to FP64 by integer bit operations with
-//    one rounding each (fix_to_f64). In FP64:
-//      n = N,  X_k = fma(s, DX_k, AX_k),  Y_k = fma(s, DY_k, AY_k),
-//    and jx, jy, sum |v|^2 f follow the pairwise ring tree of combine_rings.
+//    S = sum g, AX = g7 - g3, DX = (g0 - g4) + (g6 - g2), AY = g1 - g5, DY = (g0 - g4) - (g6 - g2).
+//    The speeds have two decimals, so with V_k = 100 v_k (integers) the momentum sums are exact
+//    integers too:
+//      N = f_0 + sum_k S_k,  Ax = sum_k V_k AX_k,  Dx = sum_k V_k DX_k  (Ay, Dy alike).
+//    These and the four S_k are converted to FP64 by integer bit operations with one rounding each
+//    (fix_to_f64). In FP64:
+//      n = N,  100 jx = fma(s, Dx, Ax),  100 jy = fma(s, Dy, Ay),
+//    and sum |v|^2 f follows the pairwise ring tree of combine_rings. The factor 1/100 is applied
+//    with 1/n (to_macro<100>).
 //  - Integer sums are associative, so the ring-parallel kernel, which adds its lanes' integers in
 //    another order, forms bit-identical moments.
 //  - A node holding an infinity or NaN (biased exponent 255) gets NaN moments, which the health
@@ -280,12 +301,14 @@ __device__ __forceinline__ int f32_exp1(float x) {
 struct FixTerm {
   int sm, p;
 };
+constexpr int FIX_TOP = 26;          // the largest term is m 2^26 < 2^50
+constexpr int FIX_E2 = 150 + FIX_TOP;  // a sum V stands for V 2^(e* - FIX_E2)
 __device__ __forceinline__ FixTerm fix_term(float x, int emax) {
   const unsigned u = __float_as_uint(x);
   const int e = (int)((u >> 23) & 0xffu);
   const int m = (int)((u & 0x7fffffu) | (e ? 0x800000u : 0u));
   const int sm = (int)(u >> 31) ? -m : m;
-  const int k = 30 - (emax - (e ? e : 1));  // <= 30
+  const int k = FIX_TOP - (emax - (e ? e : 1));  // <= FIX_TOP
   FixTerm t;
   t.sm = k >= 0 ? sm : (sm >> min(-k, 31));
   t.p = k >= 0 ? (1 << k) : 1;
@@ -295,7 +318,7 @@ __device__ __forceinline__ long long to_fix(float x, int emax) {
   const FixTerm t = fix_term(x, emax);
   return (long long)t.sm * t.p;
 }
-// V * 2^e2, rounded to nearest even, built from the integer's bits (|V| < 2^62, normal result).
+// V * 2^e2, rounded to nearest even, built from the integer's bits (|V| < 2^63, normal result).
 __device__ __forceinline__ double fix_to_f64(long long V, int e2) {
   if (V == 0) return 0.0;
   const unsigned long long sgn = V < 0 ? 0x8000000000000000ull : 0ull;
@@ -329,16 +352,23 @@ __device__ __forceinline__ RingFix ring_fix(const float (&x)[8], int emax) {
   r.DY = a - b;
   return r;
 }
-__device__ __forceinline__ void ring_from_fix(const RingFix& r, int e2, double& S, double& X, double& Y) {
-  S = fix_to_f64(r.S, e2);
-  X = fma(kS, fix_to_f64(r.DX, e2), fix_to_f64(r.AX, e2));
-  Y = fma(kS, fix_to_f64(r.DY, e2), fix_to_f64(r.AY, e2));
-}
 __device__ __forceinline__ Mom nan_moments() {
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   return Mom{nan, nan, nan, nan};
 }
 
+// n, 100 jx, 100 jy, sum |v|^2 f from the exact sums (the rings' S_k already in FP64).
+__device__ __forceinline__ Mom fix_moments(long long N, long long Ax, long long Dx, long long Ay, long long Dy,
+                                           const double (&S)[4], int e2, const Coeffs& c) {
+  Mom m;
+  m.n = fix_to_f64(N, e2);
+  m.jx = fma(kS, fix_to_f64(Dx, e2), fix_to_f64(Ax, e2));
+  m.jy = fma(kS, fix_to_f64(Dy, e2), fix_to_f64(Ay, e2));
+  m.e2 = pair_dot(c.v2[0], S[0], c.v2[1], S[1]) + pair_dot(c.v2[2], S[2], c.v2[3], S[3]);
+  return m;
+}
+
+// Moments of an FP32-storage node; jx, jy in hundredths (to_macro<100>).
 __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long long plane, long long off,
                                             const Coeffs& c) {
   float x[Q];
@@ -349,9 +379,9 @@ __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long lo
     emax = max(emax, f32_exp1(x[q]));
   }
   if (emax == 255) return nan_moments();
-  const int e2 = emax - 180;
-  long long N = to_fix(x[0], emax);
-  double S[4], X[4], Y[4];
+  const int e2 = emax - FIX_E2;
+  long long N = to_fix(x[0], emax), Ax = 0, Dx = 0, Ay = 0, Dy = 0;
+  double S[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     float g[8];
@@ -359,11 +389,13 @@ __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long lo
     for (int d = 0; d < 8; ++d) g[d] = x[1 + 8 * k + d];
     const RingFix r = ring_fix(g, emax);
     N += r.S;
-    ring_from_fix(r, e2, S[k], X[k], Y[k]);
+    Ax += speed_c(k) * r.AX;
+    Dx += speed_c(k) * r.DX;
+    Ay += speed_c(k) * r.AY;
+    Dy += speed_c(k) * r.DY;
+    S[k] = fix_to_f64(r.S, e2);
   }
-  Mom m = combine_rings(0.0, S, X, Y, c);
-  m.n = fix_to_f64(N, e2);
-  return m;
+  return fix_moments(N, Ax, Dx, Ay, Dy, S, e2, c);
 }
 
 // One ring of a node (ring-parallel kernel, FP64 storage): S, X, Y of ring k, and f_0 (read by
@@ -377,19 +409,68 @@ __device__ __forceinline__ void ring_of_node(const double* __restrict__ f, long 
   ring_sums(g, S, X, Y);
 }
 
-// Ring-parallel kernel: lane r of a quad (r = 0..3) gets S, X, Y of ring r of the quad's node and
-// the node's n, which every lane of the quad ends with. All four lanes must call it together.
-__device__ __forceinline__ void quad_ring(const double* __restrict__ f, long long plane, long long off, int r,
-                                          double& S, double& X, double& Y, double& n) {
-  double f0;
+// (n, ux, uy, T, P) from the sums; T = (sum |v|^2 f)/(2n) - |u|^2/2  (Eq. 5 with P = nT). JS is
+// the unit of jx, jy in the sums: 1 for the FP64 sums, 100 for the fixed-point ones (hundredths).
+struct Macro {
+  double n, ux, uy, T, P;
+};
+template <int JS>
+__device__ __forceinline__ Macro to_macro(const Mom& m) {
+  Macro o;
+  const double in = rcp64(m.n);
+  const double ij = JS == 1 ? in : in * (1.0 / JS);
+  o.n = m.n;
+  o.ux = m.jx * ij;
+  o.uy = m.jy * ij;
+  const double u2 = fma(o.ux, o.ux, o.uy * o.uy);
+  o.T = 0.5 * fma(m.e2, in, -u2);
+  o.P = m.n * o.T;
+  return o;
+}
+__device__ __forceinline__ Macro node_macro(const double* __restrict__ f, long long plane, long long off,
+                                            const Coeffs& c) {
+  return to_macro<1>(node_moments(f, plane, off, c));
+}
+__device__ __forceinline__ Macro node_macro(const float* __restrict__ f, long long plane, long long off,
+                                            const Coeffs& c) {
+  return to_macro<100>(node_moments(f, plane, off, c));
+}
+
+// Ring-parallel kernel: the macros of the quad's node, lane r of the quad (r = 0..3) summing ring
+// r. Every lane ends with the same values, bit for bit those of node_macro. All four lanes must
+// call it together.
+__device__ __forceinline__ Macro quad_macro(const double* __restrict__ f, long long plane, long long off, int r,
+                                            const Coeffs& c) {
+  const unsigned FULL = 0xffffffffu;
+  double f0, S, X, Y;
   ring_of_node(f, plane, off, r, f0, S, X, Y);
+  Mom m;
   // n = ((f_0 + S_0) + S_1) + (S_2 + S_3), the tree of combine_rings
   const double pn = (r == 0) ? f0 + S : S;
-  const double n2 = pn + __shfl_xor_sync(0xffffffffu, pn, 1);
-  n = n2 + __shfl_xor_sync(0xffffffffu, n2, 2);
+  const double n2 = pn + __shfl_xor_sync(FULL, pn, 1);
+  m.n = n2 + __shfl_xor_sync(FULL, n2, 2);
+  // stage 1 (lanes r, r^1): j pair = fma(v_e, X_e, v_o X_o). The even lane sends its X (Y, S),
+  // the odd lane its product v X; each then forms the pair from identical operands.
+  const bool even = (r & 1) == 0;
+  const double prodx = c.v[r] * X, prody = c.v[r] * Y, prode = c.v2[r] * S;
+  const double o_x = __shfl_xor_sync(FULL, even ? X : prodx, 1);
+  const double o_y = __shfl_xor_sync(FULL, even ? Y : prody, 1);
+  const double o_e = __shfl_xor_sync(FULL, even ? S : prode, 1);
+  const int re = r & 2;  // the even lane of the pair
+  const double jx2 = even ? fma(c.v[re], X, o_x) : fma(c.v[re], o_x, prodx);
+  const double jy2 = even ? fma(c.v[re], Y, o_y) : fma(c.v[re], o_y, prody);
+  const double e22 = even ? fma(c.v2[re], S, o_e) : fma(c.v2[re], o_e, prode);
+  // stage 2 (pairs 01 and 23): commutative sums, equal in all four lanes
+  m.jx = jx2 + __shfl_xor_sync(FULL, jx2, 2);
+  m.jy = jy2 + __shfl_xor_sync(FULL, jy2, 2);
+  m.e2 = e22 + __shfl_xor_sync(FULL, e22, 2);
+  return to_macro<1>(m);
 }
-__device__ __forceinline__ void quad_ring(const float* __restrict__ f, long long plane, long long off, int r,
-                                          double& S, double& X, double& Y, double& n) {
+// FP32 storage: each lane forms its ring's exact sums, the quad adds the integers (exact, so in
+// any order) and exchanges the four S_k, and every lane finishes as node_moments does.
+__device__ __forceinline__ Macro quad_macro(const float* __restrict__ f, long long plane, long long off, int r,
+                                            const Coeffs& c) {
+  const unsigned FULL = 0xffffffffu;
   float x[8];
   const float x0 = ld(f + off);
   int emax = f32_exp1(x0);
@@ -398,35 +479,27 @@ __device__ __forceinline__ void quad_ring(const float* __restrict__ f, long long
     x[d] = ld(f + (long long)(1 + 8 * r + d) * plane + off);
     emax = max(emax, f32_exp1(x[d]));
   }
-  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
-  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
+  emax = max(emax, __shfl_xor_sync(FULL, emax, 1));
+  emax = max(emax, __shfl_xor_sync(FULL, emax, 2));
   const RingFix rf = ring_fix(x, emax);
+  const long long V = speed_c(r);
   long long N = rf.S + (r == 0 ? to_fix(x0, emax) : 0ll);
-  N += __shfl_xor_sync(0xffffffffu, N, 1);
-  N += __shfl_xor_sync(0xffffffffu, N, 2);
-  const int e2 = emax - 180;
-  ring_from_fix(rf, e2, S, X, Y);
-  n = fix_to_f64(N, e2);
-  if (emax == 255) {
-    const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    S = X = Y = n = nan;
+  long long Ax = V * rf.AX, Dx = V * rf.DX, Ay = V * rf.AY, Dy = V * rf.DY;
+#pragma unroll
+  for (int lm = 1; lm <= 2; lm <<= 1) {
+    N += __shfl_xor_sync(FULL, N, lm);
+    Ax += __shfl_xor_sync(FULL, Ax, lm);
+    Dx += __shfl_xor_sync(FULL, Dx, lm);
+    Ay += __shfl_xor_sync(FULL, Ay, lm);
+    Dy += __shfl_xor_sync(FULL, Dy, lm);
   }
-}
-
-// (n, ux, uy, T, P) from the sums; T = (sum |v|^2 f)/(2n) - |u|^2/2  (Eq. 5 with P = nT).
-struct Macro {
-  double n, ux, uy, T, P;
-};
-__device__ __forceinline__ Macro to_macro(const Mom& m) {
-  Macro o;
-  const double in = rcp64(m.n);
-  o.n = m.n;
-  o.ux = m.jx * in;
-  o.uy = m.jy * in;
-  const double u2 = fma(o.ux, o.ux, o.uy * o.uy);
-  o.T = 0.5 * fma(m.e2, in, -u2);
-  o.P = m.n * o.T;
-  return o;
+  const int e2 = emax - FIX_E2;
+  const double Sr = fix_to_f64(rf.S, e2);
+  double S[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) S[k] = __shfl_sync(FULL, Sr, k, 4);
+  const Mom m = emax == 255 ? nan_moments() : fix_moments(N, Ax, Dx, Ay, Dy, S, e2, c);
+  return to_macro<100>(m);
 }
 
 __device__ __forceinline__ bool macro_ok(const Macro& o) {
@@ -663,7 +736,7 @@ __global__ void k_moments(const S* __restrict__ f, Grid g, Coeffs c, unsigned* _
   const int gx = blockIdx.x * blockDim.x + threadIdx.x - 1, gy = blockIdx.y * blockDim.y + threadIdx.y - 1;
   if (gx > g.nx || gy > g.ny || !ring_node_needed(g, gx, gy)) return;
   const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
-  const Macro m = to_macro(node_moments(f, g.plane, off, c));
+  const Macro m = node_macro(f, g.plane, off, c);
   if (!macro_ok(m)) atomicOr(health, H_NUMERIC);
   const MomPlanes<S> M = mom_planes<S>(g);
   M.n[off] = m.n;
@@ -717,7 +790,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
     const bool need = (inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny));
     const int cx = min(max(gx, -1), g.nx), cy = min(max(gy, -1), g.ny);  // inside the padded grid
     const long long off = (long long)(cy + NG) * g.pitch + (cx + NG);
-    const Macro m = to_macro(node_moments(f, g.plane, off, c));
+    const Macro m = node_macro(f, g.plane, off, c);
     if (need) {
       if (!macro_ok(m)) bits |= H_NUMERIC;
       s_n[ly][lx] = m.n;
@@ -818,8 +891,9 @@ __global__ void __launch_bounds__(BX * BY, MINB) k_step_batch(const BatchMember*
 
 // Ring-parallel step for small grids, where one thread per node leaves the GPU's FP64 pipes
 // waiting on long dependency chains. Four lanes share a node, lane r holding velocity ring r:
-// - Moments: each lane sums its ring. Two shuffle stages combine the rings in the same pairwise
-//   tree as node_moments, so the sums are bit for bit those of k_step.
+// - Moments (quad_macro): each lane sums its ring. With FP64 storage two shuffle stages combine
+//   the rings in the same pairwise tree as node_moments; with FP32 storage the quad adds the exact
+//   integer sums. Either way the moments are bit for bit those of k_step.
 // - Update: all four lanes evaluate the node's constants (switch, weights, f_eq site terms).
 //   That costs no extra issue slots: it is one warp instruction whether one lane or four use it.
 //   Each lane then updates its own 8 velocities, and lane 0 also the rest velocity.
@@ -849,27 +923,7 @@ __global__ void __launch_bounds__(4 * TW * TH) k_step_rp(const S* __restrict__ f
         inslot && ((inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny)));
     const int cx = min(max(gx, -1), g.nx), cy = min(max(gy, -1), g.ny);
     const long long off = (long long)(cy + NG) * g.pitch + (cx + NG);
-    double Sr, Xr, Yr, nq;
-    quad_ring(f, g.plane, off, r, Sr, Xr, Yr, nq);
-    // stage 1 (lanes r, r^1): j pair = fma(v_e, X_e, v_o X_o)
-    const bool even = (r & 1) == 0;
-    const double prodx = c.v[r] * Xr, prody = c.v[r] * Yr, prode = c.v2[r] * Sr;
-    // the even lane sends its X (Y, S), the odd lane its product v X; each then forms
-    // fma(v_even, X_even, v_odd X_odd) from identical operands
-    const double o_x = __shfl_xor_sync(FULL, even ? Xr : prodx, 1);
-    const double o_y = __shfl_xor_sync(FULL, even ? Yr : prody, 1);
-    const double o_e = __shfl_xor_sync(FULL, even ? Sr : prode, 1);
-    const int re = r & 2;  // the even lane of the pair
-    double jx2 = even ? fma(c.v[re], Xr, o_x) : fma(c.v[re], o_x, prodx);
-    double jy2 = even ? fma(c.v[re], Yr, o_y) : fma(c.v[re], o_y, prody);
-    double e22 = even ? fma(c.v2[re], Sr, o_e) : fma(c.v2[re], o_e, prode);
-    // stage 2 (pairs 01 and 23): commutative sums, equal in all four lanes
-    Mom m;
-    m.n = nq;
-    m.jx = jx2 + __shfl_xor_sync(FULL, jx2, 2);
-    m.jy = jy2 + __shfl_xor_sync(FULL, jy2, 2);
-    m.e2 = e22 + __shfl_xor_sync(FULL, e22, 2);
-    const Macro mm = to_macro(m);
+    const Macro mm = quad_macro(f, g.plane, off, r, c);
     if (need && r == 0) {
       if (!macro_ok(mm)) bits |= H_NUMERIC;
       s_n[ly][lx] = mm.n;
@@ -1001,7 +1055,7 @@ __global__ void k_macro(const S* __restrict__ f, Grid g, Coeffs c, double* __res
   const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
   if (gx >= g.nx || gy >= g.ny) return;
   const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
-  const Macro m = to_macro(node_moments(f, g.plane, off, c));
+  const Macro m = node_macro(f, g.plane, off, c);
   const long long o = (long long)gy * g.nx + gx;
   rho[o] = m.n;
   u[o] = m.ux;

@@ -123,3 +123,38 @@ def test_nonpositive_density_is_a_numerical_failure_like_the_oracle():
     o = O.Sim(nx, ny, 1e-3, 1e-3, 1e-5, 1e-5, 1.0, PER)
     o.set_macro(*fields)
     assert o.step(1) == -4
+
+
+def test_fp32_storage_rounds_every_double_to_nearest_even():
+    """Values enter FP32 storage through the kernels' integer FP64 -> FP32 conversion (the one that
+    also rounds f_eq and the pressure). Set through fdlbm_set_f and read back exactly, they equal
+    IEEE round-to-nearest-even: normals over the whole exponent range, exact ties, results in the
+    FP32 subnormal range and their ties, overflow to inf (and the tie just below 2^128), FP64
+    subnormals, signed zeros, inf and NaN."""
+    nx, ny = 64, 32
+    rng = np.random.default_rng(17)
+    n = 33 * ny * nx
+    exps = rng.integers(-170, 140, n)
+    x = rng.uniform(1.0, 2.0, n) * np.exp2(exps.astype(np.float64)) * rng.choice([-1.0, 1.0], n)
+    # exact ties: an FP32 value plus half its unit in the last place (normal and subnormal range)
+    m = rng.integers(1 << 23, 1 << 24, 4000).astype(np.float64)
+    e = rng.integers(-150, 100, 4000).astype(np.float64)
+    x[:4000] = (m + 0.5) * np.exp2(e - 23)
+    sub = rng.integers(0, 1 << 23, 2000).astype(np.float64)
+    x[4000:6000] = (sub + 0.5) * 2.0 ** -149
+    x[6000:6016] = [0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, -5e-324, 2.0 ** -150, -(2.0 ** -150),
+                    2.0 ** -150 * 1.5, 2.0 ** 128, (2 - 2.0 ** -24) * 2.0 ** 127, (2 - 2.0 ** -25) * 2.0 ** 127,
+                    2.0 ** -126 * (1 - 2.0 ** -25), 1e300, -1e300]
+    s = F.Solver(nx, ny, 1e-3, 1e-3, 1e-5, 1e-5, 1.0, PER, F.FDLBM_FP32_STORE)
+    try:
+        f = x.reshape(33, ny, nx)
+        s.set_f(f)
+        got = s.get_f()
+    finally:
+        s.close()
+    with np.errstate(over="ignore"):
+        ref = f.astype(np.float32).astype(np.float64)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan], ref[~nan])
+    assert np.array_equal(np.signbit(got[~nan]), np.signbit(ref[~nan]))

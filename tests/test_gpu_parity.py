@@ -356,7 +356,7 @@ def test_beyond_2e31_elements_per_buffer(prec):
 def test_fp32_storage_density_is_the_correctly_rounded_exact_sum():
     """FP32 storage sums a node's 33 values exactly (64-bit fixed point) and rounds once, so rho
     read back equals the exact rational sum of the stored values, correctly rounded to FP64, bit
-    for bit. This holds unless a node has a term more than 2^29 below its largest one (whose low
+    for bit. This holds unless a node has a term more than 2^25 below its largest one (whose low
     significand bits fall under the fixed-point unit), which the test checks and skips."""
     from fractions import Fraction
     w = W.riemann4q(n=96, seed=2, steps=30)
@@ -370,12 +370,68 @@ def test_fp32_storage_density_is_the_correctly_rounded_exact_sum():
         j, i = int(rng.integers(0, w.ny)), int(rng.integers(0, w.nx))
         vals = f[:, j, i]
         big = np.abs(vals).max()
-        if np.any((vals != 0) & (np.abs(vals) < big * 2.0 ** -29)):
+        if np.any((vals != 0) & (np.abs(vals) < big * 2.0 ** -25)):
             continue
         exact = sum(Fraction(float(v)) for v in vals)
         assert rho[j, i] == float(exact), (j, i)
         checked += 1
     assert checked >= 250
+
+
+def test_fp32_storage_velocity_and_temperature_are_within_ulps_of_the_exact_moments():
+    """FP32 storage forms the momentum sums exactly, weighting ring k by the integer 100 v_k (the
+    speeds (1, 1.92, 2.99, 4.49) have two decimals), and rounds only in the last few FP64 steps
+    (sqrt(1/2), 1/100, 1/n). So u, v and T read back are within a few FP64 roundings of the exact
+    moments of the stored values, here computed to 50 digits: Eqs. 3-5 with direction d of ring k
+    at angle (d + 1) pi/4. A wrong weight or direction would be off by far more."""
+    from decimal import Decimal, localcontext
+    from fractions import Fraction
+    w = W.riemann4q(n=64, seed=1, steps=20)
+    s = F.Solver.from_workload(w, F.FDLBM_FP32_STORE)
+    s.step(w.steps)
+    f = s.get_f()
+    rho, u, v, T = s.get_macro()
+    eps = np.finfo(np.float64).eps
+    speeds = [Fraction(c, 100) for c in (100, 192, 299, 449)]
+
+    def comp(x):  # a component cos or sin of a multiple of pi/4 as (rational part, sqrt(1/2) part)
+        if abs(abs(x) - 1) < 1e-9:
+            return (Fraction(int(round(x))), 0)
+        return (Fraction(0), 0) if abs(x) < 1e-9 else (Fraction(0), int(np.sign(x)))
+
+    dirs = [(comp(np.cos((d + 1) * np.pi / 4)), comp(np.sin((d + 1) * np.pi / 4))) for d in range(8)]
+    rng = np.random.default_rng(11)
+    with localcontext() as ctx:
+        ctx.prec = 50
+        h = Decimal(1) / Decimal(2).sqrt()
+
+        def dec(q):
+            return Decimal(q.numerator) / Decimal(q.denominator)
+
+        for _ in range(120):
+            j, i = int(rng.integers(0, w.ny)), int(rng.integers(0, w.nx))
+            g = [Fraction(float(x)) for x in f[:, j, i]]
+            n = sum(g)
+            ax = ay = dx = dy = e2 = Fraction(0)
+            absx = absy = abse = Fraction(0)
+            for k, vk in enumerate(speeds):
+                for d, ((xr, xs), (yr, ys)) in enumerate(dirs):
+                    fq = g[1 + 8 * k + d]
+                    ax += vk * xr * fq
+                    dx += vk * xs * fq
+                    ay += vk * yr * fq
+                    dy += vk * ys * fq
+                    e2 += vk * vk * fq
+                    absx += vk * abs(fq) * (xr != 0 or xs != 0)
+                    absy += vk * abs(fq) * (yr != 0 or ys != 0)
+                    abse += vk * vk * abs(fq)
+            ux = (dec(ax) + h * dec(dx)) / dec(n)
+            uy = (dec(ay) + h * dec(dy)) / dec(n)
+            te = dec(e2) / (2 * dec(n)) - (ux * ux + uy * uy) / 2
+            assert abs(float(Decimal(float(u[j, i])) - ux)) <= 8 * eps * float(dec(absx) / dec(n)), (j, i)
+            assert abs(float(Decimal(float(v[j, i])) - uy)) <= 8 * eps * float(dec(absy) / dec(n)), (j, i)
+            scale = float(dec(abse) / (2 * dec(n)) + (ux * ux + uy * uy) / 2)
+            assert abs(float(Decimal(float(T[j, i])) - te)) <= 32 * eps * scale, (j, i)
 
 
 @pytest.mark.parametrize("seed", [0, 1])
