@@ -20,8 +20,8 @@
 //     and only sqrt(1/2), the energy's v_k^2 and 1/100 are applied in FP64;
 //   * f_eq by the even/odd split of each opposite-direction pair: with x = p^2,
 //       nF_k E = alpha + x (beta + gamma x),  nF_k O = p (delta + eps x),  f_eq(+-) = nF_k (E +- O),
-//     where (alpha..eps) are 5 per-ring constants (7 ops per ring, 4 per pair);
-//   * dt/tau folded into nF_k, so r*f_eq costs nothing extra;
+//     where (alpha..eps) are 5 per-ring constants (6 ops per ring, 4 per pair);
+//   * dt/tau and n folded into the weights' polynomials, so r*f_eq costs nothing extra;
 //   * the Eq. 17 weights of the +-1 neighbours combined with the node's viscosity once per
 //     (axis, |c| class, ring), shared by the 2-4 directions of that class.
 #include "fdlbm_internal.h"
@@ -80,10 +80,12 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
 
 // 1/x for x in the FP32 normal range: an FP32 seed (relative error e ~ 2^-23) refined by one
 // third-order Newton step y (1 + e + e^2), e = 1 - x y, leaving O(e^3) ~ 2^-69: full FP64
-// accuracy up to the last-bit rounding, in 3 FMAs. Outside that range: IEEE division.
+// accuracy up to the last-bit rounding, in 3 FMAs. Outside that range: IEEE division, in a
+// function that is not inlined, so that its FP64 instructions never issue under a predicate.
+__device__ __noinline__ double rcp64_rare(double x) { return 1.0 / x; }
 __device__ __forceinline__ double rcp64(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), ah = hi & 0x7fffffffu;
-  if (ah - (897u << 20) >= (252u << 20)) return 1.0 / x;
+  if (__builtin_expect(ah - (897u << 20) >= (252u << 20), 0)) return rcp64_rare(x);
   const float xs = __uint_as_float(f64_to_f32_normal(ah, (unsigned)__double2loint(x)) | (hi & 0x80000000u));
   const double y = f32_to_f64_bits(__frcp_rn(xs));
   const double e = fma(-x, y, 1.0);
@@ -508,13 +510,15 @@ __device__ __forceinline__ bool macro_ok(const Macro& o) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Equilibrium constants of one node (Eqs. 10-13), with dt/tau folded in (rn = r * n).
+// Equilibrium constants of one node (Eqs. 10-13), with dt/tau folded in (r = dt/tau): 41 FP64
+// ops. F_k(theta) = theta P_k(theta) (P_k cubic) enters only as r n F_k = (r n theta) P_k(theta),
+// and the rest velocity's r f_eq = r n F_0 A0 with r n F_0 = r n - 8 sum_k r n F_k.
 struct EqSite {
-  double rn, A0, A1;       // A0 = 1 - b + b^2/2, A1 = 1 - b, b = |u|^2/(2 theta)
+  double A0, A1;           // A0 = 1 - b + b^2/2, A1 = 1 - b, b = |u|^2/(2 theta)
   double p[4];             // projections (e.u)/theta for d = 7 (x), 0 (diag), 1 (y), 2 (anti-diag)
   double x[4];             // p^2
-  double F[4];             // F_1..F_4
-  double F0;
+  double nF[4];            // r n F_1..r n F_4
+  double rest;             // r f_eq of the rest velocity
 };
 
 __device__ __forceinline__ EqSite eq_site(double n, double ux, double uy, double T, const Coeffs& c) {
@@ -528,30 +532,29 @@ __device__ __forceinline__ EqSite eq_site(double n, double ux, double uy, double
   e.p[3] = kS * (py - px);
 #pragma unroll
   for (int t = 0; t < 4; ++t) e.x[t] = e.p[t] * e.p[t];
-  const double b = 0.5 * fma(ux, ux, uy * uy) * ith;
-  e.A1 = 1.0 - b;
-  e.A0 = fma(0.5 * b, b, e.A1);
-  double sF = 0.0;
+  const double b2 = fma(ux, px, uy * py);  // 2b = |u|^2/theta
+  e.A1 = fma(-0.5, b2, 1.0);
+  e.A0 = fma(0.125 * b2, b2, e.A1);      // A1 + (2b)^2/8
+  const double rn = c.r * n, rnth = rn * th;
+  double snF = 0.0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    e.F[k] = th * fma(th, fma(th, fma(th, c.Fh[k][3], c.Fh[k][2]), c.Fh[k][1]), c.Fh[k][0]);
-    sF += e.F[k];
+    e.nF[k] = rnth * fma(th, fma(th, fma(th, c.Fh[k][3], c.Fh[k][2]), c.Fh[k][1]), c.Fh[k][0]);
+    snF += e.nF[k];
   }
-  e.F0 = fma(-8.0, sF, 1.0);
-  e.rn = c.r * n;
+  e.rest = fma(-8.0, snF, rn) * e.A0;
   return e;
 }
 
-// Per-ring constants alpha..eps (times r n F_k), 7 FP64 ops per ring: with t = r n F_k (1 - b),
+// Per-ring constants alpha..eps (times r n F_k), 6 FP64 ops per ring: with t = r n F_k (1 - b),
 //   alpha = r n F_k A0,  beta = t v_k^2/2,  gamma = r n F_k v_k^4/24,  delta = t v_k,  eps = r n F_k v_k^3/6.
 struct EqRing {
   double al, be, ga, de, ep;
 };
 __device__ __forceinline__ EqRing eq_ring(const EqSite& e, int k, const Coeffs& c) {
   EqRing r;
-  // select, not e.F[k]: k may be a run-time ring index (ring-parallel kernel)
-  const double Fk = k == 0 ? e.F[0] : k == 1 ? e.F[1] : k == 2 ? e.F[2] : e.F[3];
-  const double nF = e.rn * Fk;
+  // select, not e.nF[k]: k may be a run-time ring index (ring-parallel kernel)
+  const double nF = k == 0 ? e.nF[0] : k == 1 ? e.nF[1] : k == 2 ? e.nF[2] : e.nF[3];
   const double t = nF * e.A1;
   r.al = nF * e.A0;
   r.be = t * c.v2h[k];
@@ -834,7 +837,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
     const GhostOwn go = ghost_own(g, gx, gy);
     // rest velocity: f_eq = n F_0 A0; c = 0 on both axes (line IV only)
     {
-      const S rfeq = to_s<S>(e.rn * e.F0 * e.A0);
+      const S rfeq = to_s<S>(e.rest);
       const S* p = f + off;
       S acc = fma(w0base, ld(p), rfeq);
       acc = fma(snux, ld(p + 1) + ld(p - 1), acc);
@@ -963,7 +966,7 @@ __global__ void __launch_bounds__(4 * TW * TH) k_step_rp(const S* __restrict__ f
     const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
     const GhostOwn go = ghost_own(g, gx, gy);
     if (r == 0) {
-      const S rfeq = to_s<S>(e.rn * e.F0 * e.A0);
+      const S rfeq = to_s<S>(e.rest);
       const S* p = f + off;
       S acc = fma(w0base, ld(p), rfeq);
       acc = fma(snux, ld(p + 1) + ld(p - 1), acc);
@@ -1008,7 +1011,7 @@ __device__ __forceinline__ void write_feq(S* __restrict__ f, const Grid& g, cons
   Coeffs c = cr;
   c.r = 1.0;  // plain f_eq (no dt/tau factor)
   const EqSite e = eq_site(n, ux, uy, T, c);
-  store_node<S, 0>(f, g, gx, gy, go, from_d<S>(e.rn * e.F0 * e.A0));
+  store_node<S, 0>(f, g, gx, gy, go, from_d<S>(e.rest));
   init_ring<S, 0>(f, g, c, gx, gy, go, e);
   init_ring<S, 1>(f, g, c, gx, gy, go, e);
   init_ring<S, 2>(f, g, c, gx, gy, go, e);
