@@ -305,6 +305,8 @@ struct FixTerm {
 };
 constexpr int FIX_TOP = 26;          // the largest term is m 2^26 < 2^50
 constexpr int FIX_E2 = 150 + FIX_TOP;  // a sum V stands for V 2^(e* - FIX_E2)
+// FULL = false when the caller has checked that no term of the node needs the right shift.
+template <bool FULL = true>
 __device__ __forceinline__ FixTerm fix_term(float x, int emax) {
   const unsigned u = __float_as_uint(x);
   const int e = (int)((u >> 23) & 0xffu);
@@ -312,12 +314,18 @@ __device__ __forceinline__ FixTerm fix_term(float x, int emax) {
   const int sm = (int)(u >> 31) ? -m : m;
   const int k = FIX_TOP - (emax - (e ? e : 1));  // <= FIX_TOP
   FixTerm t;
-  t.sm = k >= 0 ? sm : (sm >> min(-k, 31));
-  t.p = k >= 0 ? (1 << k) : 1;
+  if constexpr (FULL) {
+    t.sm = k >= 0 ? sm : (sm >> min(-k, 31));
+    t.p = k >= 0 ? (1 << k) : 1;
+  } else {
+    t.sm = sm;
+    t.p = 1 << k;
+  }
   return t;
 }
+template <bool FULL = true>
 __device__ __forceinline__ long long to_fix(float x, int emax) {
-  const FixTerm t = fix_term(x, emax);
+  const FixTerm t = fix_term<FULL>(x, emax);
   return (long long)t.sm * t.p;
 }
 // V * 2^e2, rounded to nearest even, built from the integer's bits (|V| < 2^63, normal result).
@@ -338,10 +346,11 @@ __device__ __forceinline__ double fix_to_f64(long long V, int e2) {
 struct RingFix {
   long long S, AX, DX, AY, DY;
 };
+template <bool FULL = true>
 __device__ __forceinline__ RingFix ring_fix(const float (&x)[8], int emax) {
   FixTerm t[8];
 #pragma unroll
-  for (int d = 0; d < 8; ++d) t[d] = fix_term(x[d], emax);
+  for (int d = 0; d < 8; ++d) t[d] = fix_term<FULL>(x[d], emax);
   RingFix r;
   r.S = 0;
 #pragma unroll
@@ -370,26 +379,17 @@ __device__ __forceinline__ Mom fix_moments(long long N, long long Ax, long long 
   return m;
 }
 
-// Moments of an FP32-storage node; jx, jy in hundredths (to_macro<100>).
-__device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long long plane, long long off,
-                                            const Coeffs& c) {
-  float x[Q];
-  int emax = 1;
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    x[q] = ld(f + (long long)q * plane + off);
-    emax = max(emax, f32_exp1(x[q]));
-  }
-  if (emax == 255) return nan_moments();
+template <bool FULL>
+__device__ __forceinline__ Mom fix_node_moments(const float (&x)[Q], int emax, const Coeffs& c) {
   const int e2 = emax - FIX_E2;
-  long long N = to_fix(x[0], emax), Ax = 0, Dx = 0, Ay = 0, Dy = 0;
+  long long N = to_fix<FULL>(x[0], emax), Ax = 0, Dx = 0, Ay = 0, Dy = 0;
   double S[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     float g[8];
 #pragma unroll
     for (int d = 0; d < 8; ++d) g[d] = x[1 + 8 * k + d];
-    const RingFix r = ring_fix(g, emax);
+    const RingFix r = ring_fix<FULL>(g, emax);
     N += r.S;
     Ax += speed_c(k) * r.AX;
     Dx += speed_c(k) * r.DX;
@@ -398,6 +398,25 @@ __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long lo
     S[k] = fix_to_f64(r.S, e2);
   }
   return fix_moments(N, Ax, Dx, Ay, Dy, S, e2, c);
+}
+
+// Moments of an FP32-storage node; jx, jy in hundredths (to_macro<100>). When the node's values
+// all lie within 2^FIX_TOP of its largest (the usual case), no term needs the right shift and the
+// terms take the short form; the results are the same.
+__device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long long plane, long long off,
+                                            const Coeffs& c) {
+  float x[Q];
+  int emax = 1, emin = 255;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    x[q] = ld(f + (long long)q * plane + off);
+    const int e1 = f32_exp1(x[q]);
+    emax = max(emax, e1);
+    emin = min(emin, e1);
+  }
+  if (emax == 255) return nan_moments();
+  if (emax - emin <= FIX_TOP) return fix_node_moments<false>(x, emax, c);
+  return fix_node_moments<true>(x, emax, c);
 }
 
 // One ring of a node (ring-parallel kernel, FP64 storage): S, X, Y of ring k, and f_0 (read by

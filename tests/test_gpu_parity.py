@@ -378,6 +378,44 @@ def test_fp32_storage_density_is_the_correctly_rounded_exact_sum():
     assert checked >= 250
 
 
+def test_fp32_storage_density_with_far_smaller_terms():
+    """Nodes whose values span more than 2^26 take the general form of the fixed-point terms: a
+    term that far below the largest loses the bits under the sum's unit (2^-49 of the largest
+    value). Here half the nodes get a few values scaled down by 2^-30 .. 2^-70. rho read back is
+    then within 33 * 2^-49 max|f| (plus its own rounding) of the exact rational sum, and nodes
+    without such values still get the correctly rounded exact sum."""
+    from fractions import Fraction
+    nx, ny = 48, 16
+    rng = np.random.default_rng(23)
+    f = rng.uniform(0.01, 1.0, (33, ny, nx)) * rng.choice([-1.0, 1.0], (33, ny, nx), p=[0.1, 0.9])
+    f[0] += 5.0
+    tiny = rng.random((ny, nx)) < 0.5
+    for j, i in zip(*np.nonzero(tiny)):
+        qs = rng.choice(np.arange(1, 33), 4, replace=False)
+        f[qs, j, i] *= np.exp2(-rng.uniform(30, 70, 4))
+    s = F.Solver(nx, ny, 1e-3, 1e-3, 1e-5, 1e-5, 1.0, (0, 0, 0, 0), F.FDLBM_FP32_STORE)
+    try:
+        s.set_f(f)
+        g = s.get_f()                         # the stored FP32 values, widened exactly
+        rho = s.get_macro(check=False)[0]
+    finally:
+        s.close()
+    eps = np.finfo(np.float64).eps
+    spans = 0
+    for j in range(ny):
+        for i in range(nx):
+            vals = g[:, j, i]
+            big = np.abs(vals).max()
+            exact = float(sum(Fraction(float(v)) for v in vals))
+            wide = np.any((vals != 0) & (np.abs(vals) < big * 2.0 ** -27))
+            if wide:
+                spans += 1
+                assert abs(rho[j, i] - exact) <= 33 * 2.0 ** -49 * big + eps * abs(exact), (j, i)
+            elif not np.any((vals != 0) & (np.abs(vals) < big * 2.0 ** -25)):
+                assert rho[j, i] == exact, (j, i)
+    assert spans >= nx * ny // 3
+
+
 def test_fp32_storage_velocity_and_temperature_are_within_ulps_of_the_exact_moments():
     """FP32 storage forms the momentum sums exactly, weighting ring k by the integer 100 v_k (the
     speeds (1, 1.92, 2.99, 4.49) have two decimals), and rounds only in the last few FP64 steps
