@@ -272,7 +272,7 @@ __device__ __forceinline__ Mom node_moments(const double* __restrict__ f, long l
 }
 
 // FP32 storage: the moments are summed exactly in 64-bit fixed point on the integer pipes, which
-// replaces ~70 of the ~80 FP64 operations of the FP64 summation.
+// replaces ~75 of the ~80 FP64 operations of the FP64 summation.
 //  - Scale: with e* the largest biased exponent of the node's 33 values (subnormals count as 1), a
 //    value x = +-m 2^(e-150) (m its 24-bit significand) enters as the integer +-m 2^(26-e*+e): the
 //    largest value's top bit lands on bit 49. A term more than 2^26 below the largest has its
@@ -286,11 +286,11 @@ __device__ __forceinline__ Mom node_moments(const double* __restrict__ f, long l
 //    The speeds have two decimals, so with V_k = 100 v_k (integers) the momentum sums are exact
 //    integers too:
 //      N = f_0 + sum_k S_k,  Ax = sum_k V_k AX_k,  Dx = sum_k V_k DX_k  (Ay, Dy alike).
-//    These and the four S_k are converted to FP64 by integer bit operations with one rounding each
-//    (fix_to_f64). In FP64:
-//      n = N,  100 jx = fma(s, Dx, Ax),  100 jy = fma(s, Dy, Ay),
-//    and sum |v|^2 f follows the pairwise ring tree of combine_rings. The factor 1/100 is applied
-//    with 1/n (to_macro<100>).
+//    So is the energy sum, 10^4 sum |v|^2 f = sum_k V_k^2 S_k, held as two parts (energy_parts).
+//    They are converted to FP64 by integer bit operations with one rounding each (fix_to_f64).
+//    In FP64:
+//      n = N,  100 jx = fma(s, Dx, Ax),  100 jy = fma(s, Dy, Ay),  10^4 sum |v|^2 f = EH 2^32 + EL,
+//    and the factors 1/100 and 10^-4 are applied with 1/n (to_macro<100>).
 //  - Integer sums are associative, so the ring-parallel kernel, which adds its lanes' integers in
 //    another order, forms bit-identical moments.
 //  - A node holding an infinity or NaN (biased exponent 255) gets NaN moments, which the health
@@ -305,21 +305,23 @@ struct FixTerm {
 };
 constexpr int FIX_TOP = 26;          // the largest term is m 2^26 < 2^50
 constexpr int FIX_E2 = 150 + FIX_TOP;  // a sum V stands for V 2^(e* - FIX_E2)
-// FULL = false when the caller has checked that no term of the node needs the right shift.
+// FULL = false when the caller has checked that the node's values are all normal and lie within
+// 2^FIX_TOP of the largest, so that no term needs the right shift or lacks the hidden bit.
 template <bool FULL = true>
 __device__ __forceinline__ FixTerm fix_term(float x, int emax) {
   const unsigned u = __float_as_uint(x);
   const int e = (int)((u >> 23) & 0xffu);
-  const int m = (int)((u & 0x7fffffu) | (e ? 0x800000u : 0u));
-  const int sm = (int)(u >> 31) ? -m : m;
-  const int k = FIX_TOP - (emax - (e ? e : 1));  // <= FIX_TOP
   FixTerm t;
   if constexpr (FULL) {
+    const int m = (int)((u & 0x7fffffu) | (e ? 0x800000u : 0u));
+    const int sm = (int)(u >> 31) ? -m : m;
+    const int k = FIX_TOP - (emax - (e ? e : 1));  // <= FIX_TOP
     t.sm = k >= 0 ? sm : (sm >> min(-k, 31));
     t.p = k >= 0 ? (1 << k) : 1;
   } else {
-    t.sm = sm;
-    t.p = 1 << k;
+    const int m = (int)((u & 0x7fffffu) | 0x800000u);
+    t.sm = (int)(u >> 31) ? -m : m;
+    t.p = 1 << (FIX_TOP - (emax - e));
   }
   return t;
 }
@@ -368,22 +370,30 @@ __device__ __forceinline__ Mom nan_moments() {
   return Mom{nan, nan, nan, nan};
 }
 
-// n, 100 jx, 100 jy, sum |v|^2 f from the exact sums (the rings' S_k already in FP64).
+// The energy sum 10^4 sum_k v_k^2 S_k = sum_k V_k^2 S_k needs up to 71 bits, so each S_k is split
+// as hi 2^32 + lo (lo unsigned): EH = sum_k V_k^2 hi_k (|EH| < 2^41) and EL = sum_k V_k^2 lo_k
+// (< 2^52) are exact integers.
+__device__ __forceinline__ void energy_parts(int k, long long S, long long& EH, long long& EL) {
+  const long long v2 = (long long)speed_c(k) * speed_c(k);
+  EH += v2 * (long long)(int)(S >> 32);
+  EL += v2 * (long long)(unsigned)S;
+}
+// n, 100 jx, 100 jy and 10^4 sum |v|^2 f from the exact sums. EH 2^32 and EL convert to FP64
+// exactly (both below 2^53), so their one FP64 sum is the correctly rounded energy sum.
 __device__ __forceinline__ Mom fix_moments(long long N, long long Ax, long long Dx, long long Ay, long long Dy,
-                                           const double (&S)[4], int e2, const Coeffs& c) {
+                                           long long EH, long long EL, int e2) {
   Mom m;
   m.n = fix_to_f64(N, e2);
   m.jx = fma(kS, fix_to_f64(Dx, e2), fix_to_f64(Ax, e2));
   m.jy = fma(kS, fix_to_f64(Dy, e2), fix_to_f64(Ay, e2));
-  m.e2 = pair_dot(c.v2[0], S[0], c.v2[1], S[1]) + pair_dot(c.v2[2], S[2], c.v2[3], S[3]);
+  m.e2 = fix_to_f64(EH, e2 + 32) + fix_to_f64(EL, e2);
   return m;
 }
 
 template <bool FULL>
-__device__ __forceinline__ Mom fix_node_moments(const float (&x)[Q], int emax, const Coeffs& c) {
+__device__ __forceinline__ Mom fix_node_moments(const float (&x)[Q], int emax) {
   const int e2 = emax - FIX_E2;
-  long long N = to_fix<FULL>(x[0], emax), Ax = 0, Dx = 0, Ay = 0, Dy = 0;
-  double S[4];
+  long long N = to_fix<FULL>(x[0], emax), Ax = 0, Dx = 0, Ay = 0, Dy = 0, EH = 0, EL = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     float g[8];
@@ -395,14 +405,14 @@ __device__ __forceinline__ Mom fix_node_moments(const float (&x)[Q], int emax, c
     Dx += speed_c(k) * r.DX;
     Ay += speed_c(k) * r.AY;
     Dy += speed_c(k) * r.DY;
-    S[k] = fix_to_f64(r.S, e2);
+    energy_parts(k, r.S, EH, EL);
   }
-  return fix_moments(N, Ax, Dx, Ay, Dy, S, e2, c);
+  return fix_moments(N, Ax, Dx, Ay, Dy, EH, EL, e2);
 }
 
-// Moments of an FP32-storage node; jx, jy in hundredths (to_macro<100>). When the node's values
-// all lie within 2^FIX_TOP of its largest (the usual case), no term needs the right shift and the
-// terms take the short form; the results are the same.
+// Moments of an FP32-storage node; jx, jy in hundredths and the energy in 10^-4 (to_macro<100>).
+// When the node's values are all normal and lie within 2^FIX_TOP of its largest (the usual case),
+// the terms take the short form; the results are the same.
 __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long long plane, long long off,
                                             const Coeffs& c) {
   float x[Q];
@@ -410,13 +420,13 @@ __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long lo
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     x[q] = ld(f + (long long)q * plane + off);
-    const int e1 = f32_exp1(x[q]);
-    emax = max(emax, e1);
-    emin = min(emin, e1);
+    const int e = (int)((__float_as_uint(x[q]) >> 23) & 0xffu);
+    emax = max(emax, e);
+    emin = min(emin, e);
   }
   if (emax == 255) return nan_moments();
-  if (emax - emin <= FIX_TOP) return fix_node_moments<false>(x, emax, c);
-  return fix_node_moments<true>(x, emax, c);
+  if (emin > 0 && emax - emin <= FIX_TOP) return fix_node_moments<false>(x, emax);
+  return fix_node_moments<true>(x, emax);
 }
 
 // One ring of a node (ring-parallel kernel, FP64 storage): S, X, Y of ring k, and f_0 (read by
@@ -431,7 +441,8 @@ __device__ __forceinline__ void ring_of_node(const double* __restrict__ f, long 
 }
 
 // (n, ux, uy, T, P) from the sums; T = (sum |v|^2 f)/(2n) - |u|^2/2  (Eq. 5 with P = nT). JS is
-// the unit of jx, jy in the sums: 1 for the FP64 sums, 100 for the fixed-point ones (hundredths).
+// the unit of jx, jy in the sums: 1 for the FP64 sums, 100 for the fixed-point ones (hundredths,
+// with the energy sum in units of 1/JS^2).
 struct Macro {
   double n, ux, uy, T, P;
 };
@@ -440,11 +451,12 @@ __device__ __forceinline__ Macro to_macro(const Mom& m) {
   Macro o;
   const double in = rcp64(m.n);
   const double ij = JS == 1 ? in : in * (1.0 / JS);
+  const double ie = JS == 1 ? in : in * (1.0 / ((double)JS * JS));
   o.n = m.n;
   o.ux = m.jx * ij;
   o.uy = m.jy * ij;
   const double u2 = fma(o.ux, o.ux, o.uy * o.uy);
-  o.T = 0.5 * fma(m.e2, in, -u2);
+  o.T = 0.5 * fma(m.e2, ie, -u2);
   o.P = m.n * o.T;
   return o;
 }
@@ -462,36 +474,36 @@ __device__ __forceinline__ Macro node_macro(const float* __restrict__ f, long lo
 // call it together.
 __device__ __forceinline__ Macro quad_macro(const double* __restrict__ f, long long plane, long long off, int r,
                                             const Coeffs& c) {
-  const unsigned FULL = 0xffffffffu;
+  const unsigned ALL = 0xffffffffu;
   double f0, S, X, Y;
   ring_of_node(f, plane, off, r, f0, S, X, Y);
   Mom m;
   // n = ((f_0 + S_0) + S_1) + (S_2 + S_3), the tree of combine_rings
   const double pn = (r == 0) ? f0 + S : S;
-  const double n2 = pn + __shfl_xor_sync(FULL, pn, 1);
-  m.n = n2 + __shfl_xor_sync(FULL, n2, 2);
+  const double n2 = pn + __shfl_xor_sync(ALL, pn, 1);
+  m.n = n2 + __shfl_xor_sync(ALL, n2, 2);
   // stage 1 (lanes r, r^1): j pair = fma(v_e, X_e, v_o X_o). The even lane sends its X (Y, S),
   // the odd lane its product v X; each then forms the pair from identical operands.
   const bool even = (r & 1) == 0;
   const double prodx = c.v[r] * X, prody = c.v[r] * Y, prode = c.v2[r] * S;
-  const double o_x = __shfl_xor_sync(FULL, even ? X : prodx, 1);
-  const double o_y = __shfl_xor_sync(FULL, even ? Y : prody, 1);
-  const double o_e = __shfl_xor_sync(FULL, even ? S : prode, 1);
+  const double o_x = __shfl_xor_sync(ALL, even ? X : prodx, 1);
+  const double o_y = __shfl_xor_sync(ALL, even ? Y : prody, 1);
+  const double o_e = __shfl_xor_sync(ALL, even ? S : prode, 1);
   const int re = r & 2;  // the even lane of the pair
   const double jx2 = even ? fma(c.v[re], X, o_x) : fma(c.v[re], o_x, prodx);
   const double jy2 = even ? fma(c.v[re], Y, o_y) : fma(c.v[re], o_y, prody);
   const double e22 = even ? fma(c.v2[re], S, o_e) : fma(c.v2[re], o_e, prode);
   // stage 2 (pairs 01 and 23): commutative sums, equal in all four lanes
-  m.jx = jx2 + __shfl_xor_sync(FULL, jx2, 2);
-  m.jy = jy2 + __shfl_xor_sync(FULL, jy2, 2);
-  m.e2 = e22 + __shfl_xor_sync(FULL, e22, 2);
+  m.jx = jx2 + __shfl_xor_sync(ALL, jx2, 2);
+  m.jy = jy2 + __shfl_xor_sync(ALL, jy2, 2);
+  m.e2 = e22 + __shfl_xor_sync(ALL, e22, 2);
   return to_macro<1>(m);
 }
 // FP32 storage: each lane forms its ring's exact sums, the quad adds the integers (exact, so in
 // any order) and exchanges the four S_k, and every lane finishes as node_moments does.
 __device__ __forceinline__ Macro quad_macro(const float* __restrict__ f, long long plane, long long off, int r,
                                             const Coeffs& c) {
-  const unsigned FULL = 0xffffffffu;
+  const unsigned ALL = 0xffffffffu;
   float x[8];
   const float x0 = ld(f + off);
   int emax = f32_exp1(x0);
@@ -500,26 +512,25 @@ __device__ __forceinline__ Macro quad_macro(const float* __restrict__ f, long lo
     x[d] = ld(f + (long long)(1 + 8 * r + d) * plane + off);
     emax = max(emax, f32_exp1(x[d]));
   }
-  emax = max(emax, __shfl_xor_sync(FULL, emax, 1));
-  emax = max(emax, __shfl_xor_sync(FULL, emax, 2));
+  emax = max(emax, __shfl_xor_sync(ALL, emax, 1));
+  emax = max(emax, __shfl_xor_sync(ALL, emax, 2));
   const RingFix rf = ring_fix(x, emax);
   const long long V = speed_c(r);
   long long N = rf.S + (r == 0 ? to_fix(x0, emax) : 0ll);
   long long Ax = V * rf.AX, Dx = V * rf.DX, Ay = V * rf.AY, Dy = V * rf.DY;
+  long long EH = V * V * (long long)(int)(rf.S >> 32), EL = V * V * (long long)(unsigned)rf.S;
 #pragma unroll
   for (int lm = 1; lm <= 2; lm <<= 1) {
-    N += __shfl_xor_sync(FULL, N, lm);
-    Ax += __shfl_xor_sync(FULL, Ax, lm);
-    Dx += __shfl_xor_sync(FULL, Dx, lm);
-    Ay += __shfl_xor_sync(FULL, Ay, lm);
-    Dy += __shfl_xor_sync(FULL, Dy, lm);
+    N += __shfl_xor_sync(ALL, N, lm);
+    Ax += __shfl_xor_sync(ALL, Ax, lm);
+    Dx += __shfl_xor_sync(ALL, Dx, lm);
+    Ay += __shfl_xor_sync(ALL, Ay, lm);
+    Dy += __shfl_xor_sync(ALL, Dy, lm);
+    EH += __shfl_xor_sync(ALL, EH, lm);
+    EL += __shfl_xor_sync(ALL, EL, lm);
   }
   const int e2 = emax - FIX_E2;
-  const double Sr = fix_to_f64(rf.S, e2);
-  double S[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) S[k] = __shfl_sync(FULL, Sr, k, 4);
-  const Mom m = emax == 255 ? nan_moments() : fix_moments(N, Ax, Dx, Ay, Dy, S, e2, c);
+  const Mom m = emax == 255 ? nan_moments() : fix_moments(N, Ax, Dx, Ay, Dy, EH, EL, e2);
   return to_macro<100>(m);
 }
 
@@ -929,7 +940,6 @@ __global__ void __launch_bounds__(4 * TW * TH) k_step_rp(const S* __restrict__ f
   __shared__ S s_P[SH][SW];
   const int r = threadIdx.x & 3, quad = threadIdx.x >> 2;
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-  const unsigned FULL = 0xffffffffu;
   unsigned bits = 0;
 
   // Phase 1: moments on the tile and its ring; every lane takes part in every shuffle.
