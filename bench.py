@@ -45,13 +45,13 @@ sys.path.insert(0, ROOT)
 # once: ncu thread-level counts of the split step's two kernels, whose sum is the fused step's
 # work without the moments of the tile ring (see profiles/). FP32 storage sums its moments in
 # 64-bit fixed point on the integer pipes, hence the lower count (FP32 storage: 130 update +
-# 18 moments; FP64: 481 + 89).
-FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 148}
+# 15 moments; FP64: 481 + 89).
+FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145}
 # DRAM bytes (read + write) per site update of one step's launches (k_step, or k_moments +
 # k_update), by (precision, tile variant): ncu dram__bytes_read.sum + dram__bytes_write.sum of one
 # step of this bench's 4096^2 workload (single-pass capture), divided by the sites. Reported as roofline.traffic when the autotuner
 # picks the captured variant, else null.
-TRAFFIC_B_PER_SITE = {("fp32", 2): 264.3, ("fp32", 11): 467.9, ("fp64", 7): 836.7, ("fp64", 10): 873.5}
+TRAFFIC_B_PER_SITE = {("fp32", 2): 264.4, ("fp32", 11): 467.8, ("fp64", 7): 836.7, ("fp64", 10): 873.5}
 # Variants that split a step into two launches (moment pass + update pass). Their minimum bytes per
 # site update: f read twice and written once, the moment buffer (4 FP64 + P) written and read.
 SPLIT_VARIANTS = (10, 11)

@@ -333,16 +333,16 @@ __device__ __forceinline__ long long to_fix(float x, int emax) {
 // V * 2^e2, rounded to nearest even, built from the integer's bits (|V| < 2^63, normal result).
 __device__ __forceinline__ double fix_to_f64(long long V, int e2) {
   if (V == 0) return 0.0;
-  const unsigned long long sgn = V < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned long long U = V < 0 ? (unsigned long long)(-V) : (unsigned long long)V;
-  const int lz = __clzll((long long)U);
-  U <<= lz;  // leading one at bit 63
-  unsigned long long M = U >> 11;
-  const unsigned rem = (unsigned)(U & 0x7ffull);
-  M += (unsigned long long)((rem > 0x400u) | ((rem == 0x400u) & (unsigned)(M & 1ull)));
-  const unsigned long long E = (unsigned long long)(63 - lz + e2 + 1023);  // biased exponent
-  // the significand's leading one (bit 52) adds the last 1 to the exponent field; a rounding
-  // carry into bit 53 adds one more, which is the correct result
+  const unsigned long long sgn = (unsigned long long)V & 0x8000000000000000ull;
+  const unsigned long long A = V < 0 ? 0ull - (unsigned long long)V : (unsigned long long)V;
+  const int lz = __clzll((long long)A);  // >= 1
+  const unsigned long long U = A << (lz - 1);  // leading one at bit 62
+  // round to nearest even at bit 10: add 2^9 - 1 plus the lowest kept bit, then drop the 10 bits
+  // (no overflow: U < 2^63). M has its leading one at bit 52, or is 2^53 after a carry.
+  const unsigned long long M = (U + 0x1ffull + ((U >> 10) & 1ull)) >> 10;
+  const unsigned long long E = (unsigned long long)(1086 - lz + e2);  // biased exponent
+  // the leading one (bit 52) adds the last 1 to the exponent field; a carry to 2^53 adds one more,
+  // which is the correct result
   return __longlong_as_double((long long)(sgn | (((E - 1ull) << 52) + M)));
 }
 struct RingFix {
