@@ -394,10 +394,14 @@ def main():
     torch.cuda.synchronize()
     h_out = [torch.empty(a.shape, dtype=torch.float64, pin_memory=True).numpy() for a in w.macros()]
     t0 = time.perf_counter()
-    solver.set_macro(*pinned)
+    solver.set_macro(*pinned)                      # synchronous: H2D copies and f = f_eq
+    t1 = time.perf_counter()
     solver.step(args.steps)
+    solver.sync()                                  # get_macro would wait for the steps anyway
+    t2 = time.perf_counter()
     rc = F.lib().fdlbm_get_macro(solver.h, *[F._hp(a) for a in h_out])
-    t_e2e = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    t_e2e = t3 - t0
     _, _, e2e_glups = aggregate_over_ranks(t_e2e * 1e3, lups, dist, device="cuda")
     macro_bytes = 4 * w.nx * w.ny * 8
 
@@ -432,7 +436,9 @@ def main():
         "clocks": clocks,
         "e2e": {"value": e2e_glups, "unit": "GLUPS", "h2d_bytes_per_step": macro_bytes / args.steps,
                 "d2h_bytes_per_step": macro_bytes / args.steps, "status": int(rc),
-                "note": "one solve per timed region: set_macro (H2D) + %d steps + get_macro (D2H)" % args.steps},
+                "note": "one solve per timed region: set_macro (H2D) + %d steps + get_macro (D2H)" % args.steps,
+                "parts_ms": {"set_macro": round((t1 - t0) * 1e3, 2), "steps": round((t2 - t1) * 1e3, 2),
+                             "get_macro": round((t3 - t2) * 1e3, 2)}},
         "gpu_launches": args.steps * (2 if split else 1),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
