@@ -110,6 +110,12 @@ cudaError_t launch_step_f64(int variant, const void* f, void* fn, const Grid& g,
                             cudaStream_t s);
 cudaError_t launch_step_f32(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                             cudaStream_t s);
+// The tile variants (< V_TILE_COUNT) for a y-periodic grid with ny <= the tile height
+// (fdlbm_step_wrap_f32.cu, fdlbm_step_wrap_f64.cu); launch_step picks them.
+cudaError_t launch_step_wrap_f64(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
+                                 unsigned* health, cudaStream_t s);
+cudaError_t launch_step_wrap_f32(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
+                                 unsigned* health, cudaStream_t s);
 cudaError_t launch_batch_f64(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,
                              const Coeffs& c, cudaStream_t s);
 cudaError_t launch_batch_f32(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,

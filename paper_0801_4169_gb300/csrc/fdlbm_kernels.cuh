@@ -779,7 +779,10 @@ __global__ void k_moments(const S* __restrict__ f, Grid g, Coeffs c, unsigned* _
   M.P[off] = from_d<S>(m.P);
 }
 
-template <typename S, int BX, int BY, int RY, bool FROM_BUF = false>
+// WRAPY (batched kernel): a tile that holds a y-periodic grid's whole height takes its two ghost
+// rows' moments from the interior rows they copy (bit for bit the same values) instead of summing
+// them again: 4-row serving tubes in 32 x 4 tiles sum 4 rows of moments instead of 6.
+template <typename S, int BX, int BY, int RY, bool FROM_BUF = false, bool WRAPY = false>
 __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict__ fn, const Grid& g, const Coeffs& c,
                                           unsigned* __restrict__ health, int tx, int ty) {
   constexpr int TW = BX, TH = BY * RY, SW = TW + 2, SH = TH + 2, NT = BX * BY;
@@ -812,12 +815,14 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       s_P[ly][lx] = M.P[off];
     }
   } else {
+  const bool wrap = WRAPY && y0 == 0 && g.ny <= TH && g.bc[2] == BC_PERIODIC && g.bc[3] == BC_PERIODIC;
+  const int nslot = wrap ? SW * g.ny : SW * SH;  // with wrap: local rows 1..ny only
 #pragma unroll
   for (int k = 0; k < NSLOT; ++k) {
     const int idx = tid + k * NT;
     // the slots before the last always lie in the tile ring (no branch); the last one is guarded
-    if ((k + 1) * NT > SW * SH && idx >= SW * SH) continue;
-    const int lx = idx % SW, ly = idx / SW;
+    if (WRAPY ? idx >= nslot : ((k + 1) * NT > SW * SH && idx >= SW * SH)) continue;
+    const int lx = idx % SW, ly = idx / SW + (wrap ? 1 : 0);
     const int gx = x0 + lx - 1, gy = y0 + ly - 1;
     const bool inx = gx >= 0 && gx < g.nx, iny = gy >= 0 && gy < g.ny;
     const bool need = (inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny));
@@ -831,6 +836,18 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       s_uy[ly][lx] = m.uy;
       s_T[ly][lx] = m.T;
       s_P[ly][lx] = from_d<S>(m.P);
+    }
+  }
+  if (wrap) {  // CTA-uniform
+    __syncthreads();
+    // ghost row y = -1 (local row 0) copies row ny - 1 (local row ny); y = ny copies row 0
+    const int ny = g.ny;
+    for (int lx = tid; lx < SW; lx += NT) {
+      s_n[0][lx] = s_n[ny][lx], s_n[ny + 1][lx] = s_n[1][lx];
+      s_ux[0][lx] = s_ux[ny][lx], s_ux[ny + 1][lx] = s_ux[1][lx];
+      s_uy[0][lx] = s_uy[ny][lx], s_uy[ny + 1][lx] = s_uy[1][lx];
+      s_T[0][lx] = s_T[ny][lx], s_T[ny + 1][lx] = s_T[1][lx];
+      s_P[0][lx] = s_P[ny][lx], s_P[ny + 1][lx] = s_P[1][lx];
     }
   }
   }
@@ -882,10 +899,10 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
   if (bits) atomicOr(health, bits);
 }
 
-template <typename S, int BX, int BY, int RY, int MINB>
+template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false>
 __global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f, S* __restrict__ fn, Grid g, Coeffs c,
                                                   unsigned* __restrict__ health) {
-  step_tile<S, BX, BY, RY>(f, fn, g, c, health, blockIdx.x, blockIdx.y);
+  step_tile<S, BX, BY, RY, false, WRAPY>(f, fn, g, c, health, blockIdx.x, blockIdx.y);
 }
 // Split step, pass 2: the update with the tile's moments read from the moment buffer.
 template <typename S, int BX, int BY, int RY, int MINB>
@@ -919,7 +936,7 @@ __global__ void __launch_bounds__(BX * BY, MINB) k_step_batch(const BatchMember*
   const int par = (int)((m.cur0 + step) & 1ull);
   const S* in = static_cast<const S*>(m.f[par]);
   S* out = static_cast<S*>(m.f[par ^ 1]);
-  step_tile<S, BX, BY, RY>(in, out, g, c, m.health, tx, ty);
+  step_tile<S, BX, BY, RY, false, true>(in, out, g, c, m.health, tx, ty);
 }
 
 // Ring-parallel step for small grids, where one thread per node leaves the GPU's FP64 pipes
@@ -1129,12 +1146,13 @@ __global__ void k_set_f(S* __restrict__ f, Grid g, const double* __restrict__ in
 }
 
 // MINB: CTAs per SM the register allocation must allow (1 = no cap, 2 or 4 = <= 128 registers).
-template <typename S, int BX, int BY, int RY, int MINB>
+template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false>
 cudaError_t launch_step_t(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
   dim3 block(BX, BY);
   dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY * RY - 1) / (BY * RY));
-  k_step<S, BX, BY, RY, MINB><<<grid, block, 0, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g, c, health);
+  k_step<S, BX, BY, RY, MINB, WRAPY><<<grid, block, 0, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g, c,
+                                                            health);
   return cudaGetLastError();
 }
 
@@ -1195,6 +1213,24 @@ cudaError_t launch_step_v(int variant, const void* f, void* fn, const Grid& g, c
     case V_T32x32: return launch_step_t<S, 32, 8, 4, 2>(f, fn, g, c, health, s);
     case V_T32x24: return launch_step_t<S, 32, 4, 6, 4>(f, fn, g, c, health, s);
     case V_T32x28: return launch_step_t<S, 32, 4, 7, 4>(f, fn, g, c, health, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// The tile variants for a grid whose whole y-periodic height fits in one tile (step_tile WRAPY):
+// instantiated in their own translation units, fdlbm_step_wrap_*.cu.
+template <typename S>
+cudaError_t launch_step_wrap_v(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
+                               unsigned* health, cudaStream_t s) {
+  switch (variant) {
+    case V_T32x4: return launch_step_t<S, 32, 4, 1, 4, true>(f, fn, g, c, health, s);
+    case V_T32x8: return launch_step_t<S, 32, 4, 2, 4, true>(f, fn, g, c, health, s);
+    case V_T32x16: return launch_step_t<S, 32, 8, 2, 2, true>(f, fn, g, c, health, s);
+    case V_T16x4: return launch_step_t<S, 16, 4, 1, 1, true>(f, fn, g, c, health, s);
+    case V_T64x8: return launch_step_t<S, 64, 4, 2, 2, true>(f, fn, g, c, health, s);
+    case V_T32x32: return launch_step_t<S, 32, 8, 4, 2, true>(f, fn, g, c, health, s);
+    case V_T32x24: return launch_step_t<S, 32, 4, 6, 4, true>(f, fn, g, c, health, s);
+    case V_T32x28: return launch_step_t<S, 32, 4, 7, 4, true>(f, fn, g, c, health, s);
     default: return cudaErrorInvalidValue;
   }
 }
