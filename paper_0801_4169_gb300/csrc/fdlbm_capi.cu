@@ -146,7 +146,9 @@ int default_variant(const fdlbm_config* c) {
   // 16 us per step against 32 us for the tiles), and lose by 1.3x at 16 000 sites, where the
   // tiles have reached their latency floor while the ring-parallel launch is throughput-bound.
   if (sites <= 6144) return V_RP8x4;
-  if (c->ny <= 4) return V_T32x4;
+  // 4-row tubes (autotuned on a GB300, FP64 and FP32 storage): a 32 x 16 tile, whose phase 1
+  // takes one round, is fastest up to ~16 000 sites, 16 x 4 up to ~32 000, then 32 x 4.
+  if (c->ny <= 4) return sites <= 16000 ? V_T32x16 : sites <= 32000 ? V_T16x4 : V_T32x4;
   if (sites < 200000) return V_T32x8;
   return V_T32x16;
 }
