@@ -24,6 +24,8 @@
 //   * dt/tau and n folded into the weights' polynomials, so r*f_eq costs nothing extra;
 //   * the Eq. 17 weights of the +-1 neighbours combined with the node's viscosity once per
 //     (axis, |c| class, ring), shared by the 2-4 directions of that class.
+#include <atomic>
+
 #include "fdlbm_internal.h"
 
 namespace fdlbm {
@@ -734,6 +736,47 @@ __device__ __forceinline__ void update_ring(int K, const S* __restrict__ f, S* _
   store_ring<S>(fn, g, gx, gy, go, K, out);
 }
 
+// Eq. 17 for ring K's 8 velocities at one interior node, with their r f_eq given (fe[d] for
+// direction d): the staged step's second half.
+template <typename S>
+__device__ __forceinline__ void ring_stencil(int K, const S* __restrict__ f, S* __restrict__ fn, const Grid& g,
+                                             const Coeffs& c, long long off, int gx, int gy, const GhostOwn& go,
+                                             const S (&fe)[8], S w0base, S nux, S nuy) {
+  using SC = StencilConsts<S>;
+  RingW<S> w;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) w.w0[l] = w0base - SC::C2(c, K, l);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const S nu = a == 0 ? nux : nuy;
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      w.P1[a][l] = SC::W1(c, a, K, l) + nu;
+      w.M1[a][l] = SC::Wm1(c, a, K, l) + nu;
+      w.Dd[a][l] = SC::D(c, a, K, l);
+    }
+  }
+  w.nu[0] = nux;
+  w.nu[1] = nuy;
+  const S* fq = f + off;
+  S out[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const S* p = fq + (long long)(1 + 8 * K + d) * g.plane;
+    switch (d) {
+      case 0: out[0] = stencil_dir<S, 0>(p, g.pitch, w, fe[0]); break;
+      case 1: out[1] = stencil_dir<S, 1>(p, g.pitch, w, fe[1]); break;
+      case 2: out[2] = stencil_dir<S, 2>(p, g.pitch, w, fe[2]); break;
+      case 3: out[3] = stencil_dir<S, 3>(p, g.pitch, w, fe[3]); break;
+      case 4: out[4] = stencil_dir<S, 4>(p, g.pitch, w, fe[4]); break;
+      case 5: out[5] = stencil_dir<S, 5>(p, g.pitch, w, fe[5]); break;
+      case 6: out[6] = stencil_dir<S, 6>(p, g.pitch, w, fe[6]); break;
+      default: out[7] = stencil_dir<S, 7>(p, g.pitch, w, fe[7]); break;
+    }
+  }
+  store_ring<S>(fn, g, gx, gy, go, K, out);
+}
+
 template <typename S>
 __device__ __forceinline__ S to_s(double x) { return from_d<S>(x); }
 
@@ -782,9 +825,9 @@ __global__ void k_moments(const S* __restrict__ f, Grid g, Coeffs c, unsigned* _
 // WRAPY (batched kernel): a tile that holds a y-periodic grid's whole height takes its two ghost
 // rows' moments from the interior rows they copy (bit for bit the same values) instead of summing
 // them again: 4-row serving tubes in 32 x 4 tiles sum 4 rows of moments instead of 6.
-template <typename S, int BX, int BY, int RY, bool FROM_BUF = false, bool WRAPY = false>
+template <typename S, int BX, int BY, int RY, bool FROM_BUF = false, bool WRAPY = false, bool STAGE = false>
 __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict__ fn, const Grid& g, const Coeffs& c,
-                                          unsigned* __restrict__ health, int tx, int ty) {
+                                          unsigned* __restrict__ health, int tx, int ty, S* s_fe = nullptr) {
   constexpr int TW = BX, TH = BY * RY, SW = TW + 2, SH = TH + 2, NT = BX * BY;
   using SC = StencilConsts<S>;
   // P is staged in the storage precision: the switch of Eq. 16 is a limiter coefficient, and in
@@ -853,6 +896,82 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
   }
   __syncthreads();
 
+  if constexpr (STAGE) {
+    // Staged phase 2: first every node's 33 r f_eq (the FP64 work) into shared memory, s_fe[q][node],
+    // then the stencils (FP32 and memory work) from there.
+    constexpr int NN = TW * TH;
+#pragma unroll 1
+    for (int rr = 0; rr < RY; ++rr) {
+      const int lx = threadIdx.x + 1, ly = threadIdx.y + rr * BY + 1;
+      const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + rr * BY;
+      if (gx >= g.nx || gy >= g.ny) continue;
+      const int node = (threadIdx.y + rr * BY) * TW + threadIdx.x;
+      const EqSite e = eq_site(s_n[ly][lx], s_ux[ly][lx], s_uy[ly][lx], s_T[ly][lx], c);
+      s_fe[node] = to_s<S>(e.rest);
+#pragma unroll
+      for (int K = 0; K < 4; ++K) {
+        const EqRing er = eq_ring(e, K, c);
+        S fp, fm;
+        eq_pair_s<S>(er, e.p[0], e.x[0], fp, fm);
+        s_fe[(1 + 8 * K + 7) * NN + node] = fp;
+        s_fe[(1 + 8 * K + 3) * NN + node] = fm;
+        eq_pair_s<S>(er, e.p[1], e.x[1], fp, fm);
+        s_fe[(1 + 8 * K + 0) * NN + node] = fp;
+        s_fe[(1 + 8 * K + 4) * NN + node] = fm;
+        eq_pair_s<S>(er, e.p[2], e.x[2], fp, fm);
+        s_fe[(1 + 8 * K + 1) * NN + node] = fp;
+        s_fe[(1 + 8 * K + 5) * NN + node] = fm;
+        eq_pair_s<S>(er, e.p[3], e.x[3], fp, fm);
+        s_fe[(1 + 8 * K + 2) * NN + node] = fp;
+        s_fe[(1 + 8 * K + 6) * NN + node] = fm;
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int rr = 0; rr < RY; ++rr) {
+      const int lx = threadIdx.x + 1, ly = threadIdx.y + rr * BY + 1;
+      const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + rr * BY;
+      if (gx >= g.nx || gy >= g.ny) continue;
+      const int node = (threadIdx.y + rr * BY) * TW + threadIdx.x;
+      const double ux = s_ux[ly][lx], uy = s_uy[ly][lx];
+      S thx, thy;
+      if (g.flags & F_SWITCH_CONST) {
+        thx = SC::lam(c);
+        thy = SC::lam(c);
+      } else {
+        const S P0 = s_P[ly][lx];
+        const S sx = s_P[ly][lx + 1] + s_P[ly][lx - 1], sy = s_P[ly + 1][lx] + s_P[ly - 1][lx];
+        thx = SC::lam(c) * fabs(fma((S)-2, P0, sx) * recip(fma((S)2, P0, sx)));
+        thy = SC::lam(c) * fabs(fma((S)-2, P0, sy) * recip(fma((S)2, P0, sy)));
+      }
+      const S akx = fabs(from_d<S>(ux) * SC::kx(c)), aky = fabs(from_d<S>(uy) * SC::ky(c));
+      if (akx > (S)1 || aky > (S)1) bits |= H_KAPPA;
+      S snux = 0, snuy = 0;
+      if (!(g.flags & F_NO_VISC)) {
+        snux = (S)0.5 * thx * akx * ((S)1 - akx);
+        snuy = (S)0.5 * thy * aky * ((S)1 - aky);
+      }
+      const S w0base = ((S)1 - SC::r(c)) - (S)2 * (snux + snuy);
+      const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
+      const GhostOwn go = ghost_own(g, gx, gy);
+      {
+        const S* p = f + off;
+        S acc = fma(w0base, ld(p), s_fe[node]);
+        acc = fma(snux, ld(p + 1) + ld(p - 1), acc);
+        acc = fma(snuy, ld(p + g.pitch) + ld(p - g.pitch), acc);
+        store_node<S, 0>(fn, g, gx, gy, go, acc);
+      }
+#pragma unroll
+      for (int K = 0; K < 4; ++K) {
+        S fe[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) fe[d] = s_fe[(1 + 8 * K + d) * NN + node];
+        ring_stencil<S>(K, f, fn, g, c, off, gx, gy, go, fe, w0base, snux, snuy);
+      }
+    }
+    if (bits) atomicOr(health, bits);
+    return;
+  }
   // Phase 2: Eq. 17 at the tile's interior nodes.
 #pragma unroll 1
   for (int rr = 0; rr < RY; ++rr) {
@@ -899,16 +1018,29 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
   if (bits) atomicOr(health, bits);
 }
 
-template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false>
+// STAGE (FP32 storage, the 32 x 16 and 64 x 8 tiles): phase 2 goes through shared memory. The
+// tile's 33 r f_eq per node, the FP64 work, are formed first for every node and the stencils
+// follow. Dynamic shared memory of stage_bytes holds them: 66 KB beside the 22 KB of moments
+// still allows 2 CTAs per SM. Smaller tiles (4 CTAs per SM) and larger ones measured slower
+// staged; FP64 storage would need twice the bytes and does not stage.
+template <typename S, int TW, int TH, bool STAGE>
+constexpr int stage_bytes() {
+  return STAGE && sizeof(S) == 4 ? Q * TW * TH * (int)sizeof(S) : 0;
+}
+template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false, bool STAGE = false>
 __global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f, S* __restrict__ fn, Grid g, Coeffs c,
                                                   unsigned* __restrict__ health) {
-  step_tile<S, BX, BY, RY, false, WRAPY>(f, fn, g, c, health, blockIdx.x, blockIdx.y);
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  step_tile<S, BX, BY, RY, false, WRAPY, STAGE && sizeof(S) == 4>(f, fn, g, c, health, blockIdx.x, blockIdx.y,
+                                                                  reinterpret_cast<S*>(s_dyn));
 }
 // Split step, pass 2: the update with the tile's moments read from the moment buffer.
-template <typename S, int BX, int BY, int RY, int MINB>
+template <typename S, int BX, int BY, int RY, int MINB, bool STAGE = false>
 __global__ void __launch_bounds__(BX * BY, MINB) k_update(const S* __restrict__ f, S* __restrict__ fn, Grid g,
                                                     Coeffs c, unsigned* __restrict__ health) {
-  step_tile<S, BX, BY, RY, true>(f, fn, g, c, health, blockIdx.x, blockIdx.y);
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  step_tile<S, BX, BY, RY, true, false, STAGE && sizeof(S) == 4>(f, fn, g, c, health, blockIdx.x, blockIdx.y,
+                                                                 reinterpret_cast<S*>(s_dyn));
 }
 
 // Batched step: every member solve of a batch advances one time step in one launch. Members share
@@ -1146,13 +1278,32 @@ __global__ void k_set_f(S* __restrict__ f, Grid g, const double* __restrict__ in
 }
 
 // MINB: CTAs per SM the register allocation must allow (1 = no cap, 2 or 4 = <= 128 registers).
-template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false>
+// Opt a kernel in to `bytes` of dynamic shared memory (above 48 KB the default limit refuses the
+// launch), once per instantiation and device: `done` holds one bit per device ordinal.
+template <typename K>
+cudaError_t allow_dynamic_smem(K kernel, int bytes, std::atomic<unsigned long long>& done) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
+template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false, bool STAGE = false>
 cudaError_t launch_step_t(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
+  constexpr int smem = stage_bytes<S, BX, BY * RY, STAGE>();
+  static std::atomic<unsigned long long> attr{0};  // devices already opted in
+  const cudaError_t e = allow_dynamic_smem(k_step<S, BX, BY, RY, MINB, WRAPY, STAGE>, smem, attr);
+  if (e != cudaSuccess) return e;
   dim3 block(BX, BY);
   dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY * RY - 1) / (BY * RY));
-  k_step<S, BX, BY, RY, MINB, WRAPY><<<grid, block, 0, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g, c,
-                                                            health);
+  k_step<S, BX, BY, RY, MINB, WRAPY, STAGE><<<grid, block, smem, s>>>(static_cast<const S*>(f), static_cast<S*>(fn),
+                                                                      g, c, health);
   return cudaGetLastError();
 }
 
@@ -1186,14 +1337,19 @@ cudaError_t launch_rp_t(const void* f, void* fn, const Grid& g, const Coeffs& c,
   return cudaGetLastError();
 }
 
-template <typename S, int BX, int BY, int RY, int MINB>
+template <typename S, int BX, int BY, int RY, int MINB, bool STAGE = false>
 cudaError_t launch_split_t(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health, cudaStream_t s) {
   if (!g.mom) return cudaErrorInvalidValue;
+  constexpr int smem = stage_bytes<S, BX, BY * RY, STAGE>();
+  static std::atomic<unsigned long long> attr{0};  // devices already opted in
+  const cudaError_t e = allow_dynamic_smem(k_update<S, BX, BY, RY, MINB, STAGE>, smem, attr);
+  if (e != cudaSuccess) return e;
   dim3 mb(32, 8), mg((g.nx + 2 + 31) / 32, (g.ny + 2 + 7) / 8);
   k_moments<S><<<mg, mb, 0, s>>>(static_cast<const S*>(f), g, c, health);
   dim3 block(BX, BY);
   dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY * RY - 1) / (BY * RY));
-  k_update<S, BX, BY, RY, MINB><<<grid, block, 0, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g, c, health);
+  k_update<S, BX, BY, RY, MINB, STAGE><<<grid, block, smem, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g,
+                                                                 c, health);
   return cudaGetLastError();
 }
 
@@ -1201,15 +1357,15 @@ template <typename S>
 cudaError_t launch_step_v(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
   switch (variant) {
-    case V_S32x16: return launch_split_t<S, 32, 8, 2, 2>(f, fn, g, c, health, s);
+    case V_S32x16: return launch_split_t<S, 32, 8, 2, 2, true>(f, fn, g, c, health, s);
     case V_S32x32: return launch_split_t<S, 32, 8, 4, 2>(f, fn, g, c, health, s);
     case V_RP16x4: return launch_rp_t<S, 16, 4>(f, fn, g, c, health, s);
     case V_RP8x4: return launch_rp_t<S, 8, 4>(f, fn, g, c, health, s);
     case V_T32x4: return launch_step_t<S, 32, 4, 1, 4>(f, fn, g, c, health, s);
     case V_T32x8: return launch_step_t<S, 32, 4, 2, 4>(f, fn, g, c, health, s);
-    case V_T32x16: return launch_step_t<S, 32, 8, 2, 2>(f, fn, g, c, health, s);
+    case V_T32x16: return launch_step_t<S, 32, 8, 2, 2, false, true>(f, fn, g, c, health, s);
     case V_T16x4: return launch_step_t<S, 16, 4, 1, 1>(f, fn, g, c, health, s);
-    case V_T64x8: return launch_step_t<S, 64, 4, 2, 2>(f, fn, g, c, health, s);
+    case V_T64x8: return launch_step_t<S, 64, 4, 2, 2, false, true>(f, fn, g, c, health, s);
     case V_T32x32: return launch_step_t<S, 32, 8, 4, 2>(f, fn, g, c, health, s);
     case V_T32x24: return launch_step_t<S, 32, 4, 6, 4>(f, fn, g, c, health, s);
     case V_T32x28: return launch_step_t<S, 32, 4, 7, 4>(f, fn, g, c, health, s);
@@ -1225,9 +1381,9 @@ cudaError_t launch_step_wrap_v(int variant, const void* f, void* fn, const Grid&
   switch (variant) {
     case V_T32x4: return launch_step_t<S, 32, 4, 1, 4, true>(f, fn, g, c, health, s);
     case V_T32x8: return launch_step_t<S, 32, 4, 2, 4, true>(f, fn, g, c, health, s);
-    case V_T32x16: return launch_step_t<S, 32, 8, 2, 2, true>(f, fn, g, c, health, s);
+    case V_T32x16: return launch_step_t<S, 32, 8, 2, 2, true, true>(f, fn, g, c, health, s);
     case V_T16x4: return launch_step_t<S, 16, 4, 1, 1, true>(f, fn, g, c, health, s);
-    case V_T64x8: return launch_step_t<S, 64, 4, 2, 2, true>(f, fn, g, c, health, s);
+    case V_T64x8: return launch_step_t<S, 64, 4, 2, 2, true, true>(f, fn, g, c, health, s);
     case V_T32x32: return launch_step_t<S, 32, 8, 4, 2, true>(f, fn, g, c, health, s);
     case V_T32x24: return launch_step_t<S, 32, 4, 6, 4, true>(f, fn, g, c, health, s);
     case V_T32x28: return launch_step_t<S, 32, 4, 7, 4, true>(f, fn, g, c, health, s);
