@@ -822,6 +822,31 @@ __global__ void k_moments(const S* __restrict__ f, Grid g, Coeffs c, unsigned* _
   M.P[off] = from_d<S>(m.P);
 }
 
+// The 33 r f_eq of one node into a stage s_fe[q][node] (NN nodes per plane).
+template <typename S, int NN>
+__device__ __forceinline__ void stage_feq(S* __restrict__ s_fe, int node, double n, double ux, double uy, double T,
+                                          const Coeffs& c) {
+  const EqSite e = eq_site(n, ux, uy, T, c);
+  s_fe[node] = to_s<S>(e.rest);
+#pragma unroll
+  for (int K = 0; K < 4; ++K) {
+    const EqRing er = eq_ring(e, K, c);
+    S fp, fm;
+    eq_pair_s<S>(er, e.p[0], e.x[0], fp, fm);
+    s_fe[(1 + 8 * K + 7) * NN + node] = fp;
+    s_fe[(1 + 8 * K + 3) * NN + node] = fm;
+    eq_pair_s<S>(er, e.p[1], e.x[1], fp, fm);
+    s_fe[(1 + 8 * K + 0) * NN + node] = fp;
+    s_fe[(1 + 8 * K + 4) * NN + node] = fm;
+    eq_pair_s<S>(er, e.p[2], e.x[2], fp, fm);
+    s_fe[(1 + 8 * K + 1) * NN + node] = fp;
+    s_fe[(1 + 8 * K + 5) * NN + node] = fm;
+    eq_pair_s<S>(er, e.p[3], e.x[3], fp, fm);
+    s_fe[(1 + 8 * K + 2) * NN + node] = fp;
+    s_fe[(1 + 8 * K + 6) * NN + node] = fm;
+  }
+}
+
 // WRAPY (batched kernel): a tile that holds a y-periodic grid's whole height takes its two ghost
 // rows' moments from the interior rows they copy (bit for bit the same values) instead of summing
 // them again: 4-row serving tubes in 32 x 4 tiles sum 4 rows of moments instead of 6.
@@ -906,25 +931,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + rr * BY;
       if (gx >= g.nx || gy >= g.ny) continue;
       const int node = (threadIdx.y + rr * BY) * TW + threadIdx.x;
-      const EqSite e = eq_site(s_n[ly][lx], s_ux[ly][lx], s_uy[ly][lx], s_T[ly][lx], c);
-      s_fe[node] = to_s<S>(e.rest);
-#pragma unroll
-      for (int K = 0; K < 4; ++K) {
-        const EqRing er = eq_ring(e, K, c);
-        S fp, fm;
-        eq_pair_s<S>(er, e.p[0], e.x[0], fp, fm);
-        s_fe[(1 + 8 * K + 7) * NN + node] = fp;
-        s_fe[(1 + 8 * K + 3) * NN + node] = fm;
-        eq_pair_s<S>(er, e.p[1], e.x[1], fp, fm);
-        s_fe[(1 + 8 * K + 0) * NN + node] = fp;
-        s_fe[(1 + 8 * K + 4) * NN + node] = fm;
-        eq_pair_s<S>(er, e.p[2], e.x[2], fp, fm);
-        s_fe[(1 + 8 * K + 1) * NN + node] = fp;
-        s_fe[(1 + 8 * K + 5) * NN + node] = fm;
-        eq_pair_s<S>(er, e.p[3], e.x[3], fp, fm);
-        s_fe[(1 + 8 * K + 2) * NN + node] = fp;
-        s_fe[(1 + 8 * K + 6) * NN + node] = fm;
-      }
+      stage_feq<S, NN>(s_fe, node, s_n[ly][lx], s_ux[ly][lx], s_uy[ly][lx], s_T[ly][lx], c);
     }
     __syncthreads();
 #pragma unroll 1
@@ -969,9 +976,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
         ring_stencil<S>(K, f, fn, g, c, off, gx, gy, go, fe, w0base, snux, snuy);
       }
     }
-    if (bits) atomicOr(health, bits);
-    return;
-  }
+  } else {
   // Phase 2: Eq. 17 at the tile's interior nodes.
 #pragma unroll 1
   for (int rr = 0; rr < RY; ++rr) {
@@ -1014,6 +1019,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
     update_ring<S>(1, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
     update_ring<S>(2, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
     update_ring<S>(3, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+  }
   }
   if (bits) atomicOr(health, bits);
 }
