@@ -1,7 +1,8 @@
 #pragma once
 // fdlbm_kernels.cuh -- sm_103a kernels of the FDLBM step (Gan, Xu, Zhang, Yu, Li, arXiv 0801.4169).
-// Included by fdlbm_step_f64.cu / fdlbm_step_f32.cu (one precision each, compiled in parallel)
-// and fdlbm_aux.cu (initial condition, boundary, moment and copy kernels).
+// Included by fdlbm_step_f64.cu / fdlbm_step_f32.cu (one precision each, compiled in parallel),
+// fdlbm_step_wrap_*.cu (tiles that hold a periodic grid's height) and fdlbm_aux.cu (initial
+// condition, boundary, moment and copy kernels).
 //
 // One fused kernel per time step computes, for every interior node of its tile:
 //   moments n, u, T, P of Eqs. 3-5            (tile + 1-node ring, staged in shared memory; FP64
@@ -10,14 +11,16 @@
 //   weights F_k(theta) (Eqs. 11-13) and f_eq (Eq. 10)        (FP64)
 //   Eq. 17 for all 33 velocities, both axes, relaxation once  (storage precision)
 // and writes f_new plus the ghost copies it owns (periodic wrap, zero-gradient copy, specular
-// mirror), so the next step needs no separate boundary pass.
+// mirror), so the next step needs no separate boundary pass. With FP32 storage the 32 x 16 and
+// 64 x 8 tiles stage the f_eq of all their nodes in shared memory first and run the stencils after
+// (STAGE), so that each warp's FP64 work comes in one dense stretch.
 //
 // On this GPU an FP64 instruction (including an FP32<->FP64 conversion) issues at 2/clk/SM, ~64x
 // below FP32, so the step is bound by the FP64 pipe, not by HBM. The code is arranged to issue as
 // few FP64 operations per node as the method allows:
 //   * ring moments from shared differences (S, X, Y per ring: 15 ops with FP64 storage); with
-//     FP32 storage the ring sums and the speed-weighted momentum sums are exact 64-bit integers,
-//     and only sqrt(1/2), the energy's v_k^2 and 1/100 are applied in FP64;
+//     FP32 storage the ring, speed-weighted momentum and energy sums are exact 64-bit integers,
+//     and only sqrt(1/2), the two energy parts' sum and 1/100, 10^-4 are applied in FP64;
 //   * f_eq by the even/odd split of each opposite-direction pair: with x = p^2,
 //       nF_k E = alpha + x (beta + gamma x),  nF_k O = p (delta + eps x),  f_eq(+-) = nF_k (E +- O),
 //     where (alpha..eps) are 5 per-ring constants (6 ops per ring, 4 per pair);
