@@ -51,7 +51,7 @@ FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145}
 # k_update), by (precision, tile variant): ncu dram__bytes_read.sum + dram__bytes_write.sum of one
 # step of this bench's 4096^2 workload (single-pass capture), divided by the sites. Reported as roofline.traffic when the autotuner
 # picks the captured variant, else null.
-TRAFFIC_B_PER_SITE = {("fp32", 2): 268.2, ("fp32", 11): 467.8, ("fp64", 7): 836.7, ("fp64", 10): 873.5}
+TRAFFIC_B_PER_SITE = {("fp32", 2): 268.5, ("fp32", 11): 467.8, ("fp64", 7): 836.7, ("fp64", 10): 873.5}
 # Variants that split a step into two launches (moment pass + update pass). Their minimum bytes per
 # site update: f read twice and written once, the moment buffer (4 FP64 + P) written and read.
 SPLIT_VARIANTS = (10, 11)
