@@ -3,8 +3,11 @@
 Such a caller (its device memory all belongs to another allocator, or its path must not call
 cudaMalloc) owns both state buffers; the entry point keeps its only scratch, one health word
 per step, in a static device array. These tests check it against the handle path
-(fdlbm_step) on two calls in a row, within the f-level tolerance the parity tests use, and
-check its size limit and its report of the failing step.
+(fdlbm_step) on two calls in a row, within the f-level tolerance the parity tests use, on grids
+that take each kind of launch the entry point can pick (ring-parallel for small grids, the 32 x 8
+tile, the 32 x 16 tile that stages f_eq in dynamic shared memory, a tile holding a periodic tube's
+height), check that a call changes the device's free memory by nothing, and check its size limit
+and its report of the failing step.
 """
 import numpy as np
 import pytest
@@ -53,9 +56,22 @@ def _copies(solver):
     return bufs
 
 
-@pytest.mark.parametrize("prec", [F.FDLBM_FP64, F.FDLBM_FP32_STORE])
-def test_noalloc_matches_handle_on_two_calls(prec):
-    w = W.reflection(nx=300, ny=75) if prec == F.FDLBM_FP64 else W.riemann4q(n=128)
+# (workload, precision): the launch each grid takes is the library's default for its size
+CASES = {
+    "ring_parallel_4096_fp64": (lambda: W.riemann4q(n=64), F.FDLBM_FP64),          # <= 6144 sites
+    "ring_parallel_4096_fp32": (lambda: W.riemann4q(n=64), F.FDLBM_FP32_STORE),
+    "tile32x8_reflection_fp64": (lambda: W.reflection(nx=300, ny=75), F.FDLBM_FP64),  # 22 500 sites
+    "tile32x8_riemann_fp32": (lambda: W.riemann4q(n=128), F.FDLBM_FP32_STORE),
+    "tube_wrap_4000x4_fp64": (lambda: W.shock_tube(nx=4000, ny=4), F.FDLBM_FP64),     # 4-row tube
+    "staged32x16_262144_fp32": (lambda: W.riemann4q(n=512), F.FDLBM_FP32_STORE),    # > 200 000 sites
+    "tile32x16_262144_fp64": (lambda: W.riemann4q(n=512), F.FDLBM_FP64),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_noalloc_matches_handle_on_two_calls(case):
+    make, prec = CASES[case]
+    w = make()
     s = F.Solver.from_workload(w, prec)
     a, b = _copies(s)
     # call 1: 7 steps, result in the second buffer (odd count)
@@ -72,6 +88,23 @@ def test_noalloc_matches_handle_on_two_calls(prec):
     torch.cuda.synchronize()
     got = _interior(b, s.cfg)
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.abs(ref).max()
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [F.FDLBM_FP64, F.FDLBM_FP32_STORE])
+def test_noalloc_call_leaves_free_device_memory_unchanged(prec):
+    """After a first call (which may load the module and look up the scratch address), a call
+    on a grid that takes the staged 32 x 16 tile changes the device's free memory by 0 bytes."""
+    w = W.riemann4q(n=512)
+    s = F.Solver.from_workload(w, prec)
+    a, b = _copies(s)
+    assert F.fdlbm_step_noalloc(s.cfg, a, b, 2) == -1
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert F.fdlbm_step_noalloc(s.cfg, a, b, 3) == -1
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
     s.close()
 
 
