@@ -72,8 +72,20 @@ enum fdlbm_side { FDLBM_LEFT = 0, FDLBM_RIGHT = 1, FDLBM_BOTTOM = 2, FDLBM_TOP =
 /* Storage / arithmetic precision.
  *  FP64        f stored in FP64; moments, f_eq and the stencil in FP64.
  *  FP32_STORE  f stored and differenced in FP32; moments (Eqs. 3-5), weights and
- *              f_eq (Eqs. 10-13) evaluated in FP64. */
-enum fdlbm_prec { FDLBM_FP64 = 0, FDLBM_FP32_STORE = 1 };
+ *              f_eq (Eqs. 10-13) evaluated in FP64. Its rounding error is about
+ *              kappa * 2^-24 * n per step, kappa = sum |f_eq| / n, which destroys the
+ *              temperature at high Mach number (kappa ~ 1e4 - 1e9).
+ *  FNEQ32      f stored as its departure from the local equilibrium: per node the macros
+ *              (n, u, v, T) in FP64 and g = f - f_eq(n, u, v, T) (Eq. 10) in FP32. Each step
+ *              rebuilds f = f_eq + g in FP64 over the tile and its halo, applies Eq. 17 in
+ *              FP64, takes the new moments (Eqs. 3-5) in FP64 and stores the new g. The
+ *              rounding error is then 2^-24 |g| instead of 2^-24 |f|: small where the flow is
+ *              near equilibrium, at any Mach number. 164 bytes per node and buffer, against
+ *              264 (FP64) and 132 (FP32_STORE); about 1.6x the FP64 path's FP64 work.
+ *              fdlbm_get_macro returns the stored macros; fdlbm_get_f returns f_eq + g;
+ *              fdlbm_set_f stores the FP64 moments of the given f and its departure from their
+ *              equilibrium. Not accepted by fdlbm_batch_add. */
+enum fdlbm_prec { FDLBM_FP64 = 0, FDLBM_FP32_STORE = 1, FDLBM_FNEQ32 = 2 };
 
 /* Scheme variants of Sec. 4 (Fig. 2, Fig. 3): drop line II, III or IV of Eq. 17,
  * or hold the switch theta_alphaI of Eq. 16 at lambda. Default 0 = full Eq. 17. */
@@ -171,7 +183,8 @@ int fdlbm_save(fdlbm_t h, const char* path);
 int fdlbm_load(fdlbm_t h, const char* path);
 
 /* Launch variants of the fused step (CTA tile shapes). Every variant gives bitwise identical
- * results: a node's arithmetic does not depend on the tiling. */
+ * results: a node's arithmetic does not depend on the tiling. FDLBM_FNEQ32 has its own kernel and
+ * maps the variants onto its tile shapes (32x4, 32x8 at two register caps, 16x16, 64x4). */
 int fdlbm_variant_count(void);
 int fdlbm_set_variant(fdlbm_t h, int variant);  /* FDLBM_E_ARG if out of range */
 int fdlbm_get_variant(fdlbm_t h);               /* current variant, or a negative status */
@@ -318,8 +331,10 @@ const char* fdlbm_server_last_error(fdlbm_server_t s);
  * cfg      the problem (as for fdlbm_create_ex).
  * f_a      the current state, in the layout the handle calls use: 33 planes f[q][j+2][i+2] of
  *          (ny+4) rows x pitch elements, pitch = (nx+4) rounded up to a multiple of 32, in the
- *          storage precision of cfg->prec. Device memory, 256-byte aligned. Its ghost ring must
- *          be filled (e.g. it was produced by a handle, or copied from one).
+ *          storage precision of cfg->prec (FDLBM_FNEQ32: 33 FP32 planes of g, then, from the next
+ *          256-byte boundary, 4 FP64 planes n, u, v, T of the same shape). Device memory,
+ *          256-byte aligned. Its ghost ring must be filled (e.g. it was produced by a handle, or
+ *          copied from one).
  * f_b      the second buffer of the pair, same size and alignment, with the same Dirichlet
  *          ghosts as f_a (steps rewrite every other ghost).
  * nsteps   0..FDLBM_NOALLOC_MAX_STEPS; larger values return FDLBM_E_ARG. Steps alternate
@@ -329,7 +344,10 @@ const char* fdlbm_server_last_error(fdlbm_server_t s);
  * cuda_stream  a cudaStream_t or NULL; the call synchronises it before returning.
  *
  * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture. Every call on a
+ * with that device current, and later calls reuse it; make that first call before any stream
+ * capture. cudaDeviceReset unloads the library's device code and may place the array elsewhere
+ * when it is loaded again, so the remembered address is then stale: do not call
+ * fdlbm_step_noalloc in a process after it has reset the device. Every call on a
  * device shares the one array and clears the words it uses at its start: calls that overlap on
  * the GPU (different streams or threads) race on it. Errors: FDLBM_E_ARG (invalid cfg, NULL or
  * misaligned buffers, nsteps out of range), FDLBM_E_NUMERIC, FDLBM_E_CUDA; the message is in

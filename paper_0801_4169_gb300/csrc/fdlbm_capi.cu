@@ -52,7 +52,10 @@ bool valid_cfg(const fdlbm_config* c, std::string* why) {
   if ((long long)c->nx * c->ny > (1LL << 31)) { *why = "nx*ny too large"; return false; }
   if (!(c->dx > 0) || !(c->dy > 0) || !(c->dt > 0) || !(c->tau > 0)) { *why = "dx, dy, dt, tau must be > 0"; return false; }
   if (!(c->lambda >= 0) || !std::isfinite(c->lambda)) { *why = "lambda must be finite and >= 0"; return false; }
-  if (c->prec != FDLBM_FP64 && c->prec != FDLBM_FP32_STORE) { *why = "prec must be FDLBM_FP64 or FDLBM_FP32_STORE"; return false; }
+  if (c->prec != FDLBM_FP64 && c->prec != FDLBM_FP32_STORE && c->prec != FDLBM_FNEQ32) {
+    *why = "prec must be FDLBM_FP64, FDLBM_FP32_STORE or FDLBM_FNEQ32";
+    return false;
+  }
   if (c->flags & ~15) { *why = "unknown flag bits"; return false; }
   for (int s = 0; s < 4; ++s)
     if (c->bc[s] < 0 || c->bc[s] > 3) { *why = "boundary kind out of range"; return false; }
@@ -74,11 +77,17 @@ Layout layout_of(const fdlbm_config* c) {
   L.g.flags = c->flags;
   L.esize = c->prec == FDLBM_FP64 ? 8 : 4;
   L.fbytes = round_up((size_t)Q * L.g.plane * L.esize, 256);
+  L.g.aux_off = 0;
+  if (c->prec == FDLBM_FNEQ32) {  // 33 FP32 planes of g, then 4 FP64 planes n, ux, uy, T
+    L.g.aux_off = (long long)L.fbytes;
+    L.fbytes = round_up(L.fbytes + (size_t)4 * L.g.plane * sizeof(double), 256);
+  }
   L.health_off = 2 * L.fbytes;
   L.stage_off = L.health_off + 256;
   L.mom_off = L.stage_off + round_up((size_t)4 * c->nx * c->ny * sizeof(double), 256);
   // moment buffer of the split step: 4 FP64 planes + P in the storage precision
-  L.mom_bytes = (long long)c->nx * c->ny > 65536 ? round_up((size_t)L.g.plane * (4 * sizeof(double) + L.esize), 256) : 0;
+  L.mom_bytes = (long long)c->nx * c->ny > 65536 && c->prec != FDLBM_FNEQ32
+                    ? round_up((size_t)L.g.plane * (4 * sizeof(double) + L.esize), 256) : 0;
   L.total = L.mom_off + L.mom_bytes;
   L.g.mom = nullptr;  // set to the handle's buffer once its memory is known
   return L;
@@ -142,6 +151,7 @@ Coeffs make_coeffs(const fdlbm_config* cfg) {
 
 int default_variant(const fdlbm_config* c) {
   const long long sites = (long long)c->nx * c->ny;
+  if (c->prec == FDLBM_FNEQ32) return c->ny <= 4 ? V_T32x4 : V_T32x8;  // its own kernel (fdlbm_fneq.cu)
   // Small grids are latency-bound: four lanes per node win up to a few thousand sites (400 x 4:
   // 16 us per step against 32 us for the tiles), and lose by 1.3x at 16 000 sites, where the
   // tiles have reached their latency floor while the ring-parallel launch is throughput-bound.
@@ -185,7 +195,9 @@ int enqueue_health_copy(fdlbm_ctx* h) {
 
 int fill_ghosts_dirichlet(fdlbm_ctx* h) {
   for (int b = 0; b < 2; ++b) {
-    cudaError_t e = launch_dirichlet(h->cfg.prec, h->f[b], h->grid, h->coeffs, h->bstate, h->stream);
+    cudaError_t e = h->cfg.prec == FDLBM_FNEQ32 ? launch_dirichlet_fneq(h->f[b], h->grid, h->bstate, h->stream)
+                                                : launch_dirichlet(h->cfg.prec, h->f[b], h->grid, h->coeffs, h->bstate,
+                                                                   h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "dirichlet launch");
   }
   return FDLBM_OK;
@@ -197,7 +209,8 @@ int init_from_device_macros(fdlbm_ctx* h, const double* rho, const double* u, co
   if (e != cudaSuccess) return cuda_fail(h, e, "health reset");
   // both buffers get f_eq so ghost regions never hold stale data
   for (int b = 0; b < 2; ++b) {
-    e = launch_init(h->cfg.prec, h->f[b], h->grid, h->coeffs, rho, u, v, T, h->stream);
+    e = h->cfg.prec == FDLBM_FNEQ32 ? launch_init_fneq(h->f[b], h->grid, h->coeffs, rho, u, v, T, h->stream)
+                                    : launch_init(h->cfg.prec, h->f[b], h->grid, h->coeffs, rho, u, v, T, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "init launch");
   }
   int rc = fill_ghosts_dirichlet(h);
@@ -405,7 +418,8 @@ int fdlbm_get_macro_device(fdlbm_t h, double* rho, double* u, double* v, double*
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (!rho || !u || !v || !T) return fail(h, FDLBM_E_ARG, "NULL macro array");
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "no state yet");
-  cudaError_t e = launch_macro(h->cfg.prec, h->f[h->cur], h->grid, rho, u, v, T, h->stream);
+  cudaError_t e = h->cfg.prec == FDLBM_FNEQ32 ? launch_macro_fneq(h->f[h->cur], h->grid, rho, u, v, T, h->stream)
+                                              : launch_macro(h->cfg.prec, h->f[h->cur], h->grid, rho, u, v, T, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "macro launch");
   return FDLBM_OK;
 }
@@ -435,7 +449,10 @@ int fdlbm_get_f(fdlbm_t h, double* f) {
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "no state yet");
   int rc = ensure_fstage(h, full_f_doubles(h));
   if (rc) return rc;
-  cudaError_t e = launch_get_f(h->cfg.prec, h->f[h->cur], h->grid, h->d_fstage, h->stream);
+  cudaError_t e = h->cfg.prec == FDLBM_FNEQ32
+                      ? launch_get_region_fneq(h->f[h->cur], h->grid, h->coeffs, 0, 0, h->cfg.nx, h->cfg.ny,
+                                               h->d_fstage, h->stream)
+                      : launch_get_f(h->cfg.prec, h->f[h->cur], h->grid, h->d_fstage, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_f launch");
   e = cudaMemcpyAsync(f, h->d_fstage, (size_t)Q * h->cfg.nx * h->cfg.ny * sizeof(double), cudaMemcpyDeviceToHost,
                       h->stream);
@@ -457,7 +474,9 @@ int fdlbm_get_f_region(fdlbm_t h, int x0, int y0, int w, int hgt, double* f) {
   const size_t nd = (size_t)Q * w * hgt;
   int rc = ensure_fstage(h, nd);
   if (rc) return rc;
-  cudaError_t e = launch_get_region(h->cfg.prec, h->f[h->cur], h->grid, x0, y0, w, hgt, h->d_fstage, h->stream);
+  cudaError_t e = h->cfg.prec == FDLBM_FNEQ32
+                      ? launch_get_region_fneq(h->f[h->cur], h->grid, h->coeffs, x0, y0, w, hgt, h->d_fstage, h->stream)
+                      : launch_get_region(h->cfg.prec, h->f[h->cur], h->grid, x0, y0, w, hgt, h->d_fstage, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_f_region launch");
   e = cudaMemcpyAsync(f, h->d_fstage, nd * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_f_region copy");
@@ -479,7 +498,8 @@ int fdlbm_set_f(fdlbm_t h, const double* f) {
     if (e != cudaSuccess) return cuda_fail(h, e, "set_f clear");
   }
   for (int b = 0; b < 2; ++b) {
-    e = launch_set_f(h->cfg.prec, h->f[b], h->grid, h->d_fstage, h->stream);
+    e = h->cfg.prec == FDLBM_FNEQ32 ? launch_set_f_fneq(h->f[b], h->grid, h->coeffs, h->d_fstage, h->stream)
+                                    : launch_set_f(h->cfg.prec, h->f[b], h->grid, h->d_fstage, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_f launch");
   }
   rc = fill_ghosts_dirichlet(h);

@@ -43,6 +43,9 @@ struct Grid {
   // Moment buffer of the split step (V_S* variants), or null: planes n, ux, uy, T (FP64) and P
   // (storage precision) over the padded grid, indexed like f. Only grids above 65 536 sites have one.
   void* mom;
+  // FDLBM_FNEQ32 only: byte offset, within one state buffer, of its 4 FP64 planes n, ux, uy, T
+  // (after the 33 FP32 planes of g = f - f_eq); 0 for the other precisions.
+  long long aux_off;
 };
 
 // Per-solve constants computed once on the host in FP64 and passed by value (kernel parameter
@@ -104,8 +107,8 @@ enum StepVariant {
 };
 inline bool variant_needs_mom(int v) { return v == V_S32x16 || v == V_S32x32; }
 
-// Kernel launchers (fdlbm_aux.cu, fdlbm_step_f32.cu, fdlbm_step_f64.cu). All return
-// cudaGetLastError() of the launch.
+// Kernel launchers (fdlbm_aux.cu, fdlbm_step_f32.cu, fdlbm_step_f64.cu, fdlbm_fneq.cu). All return
+// cudaGetLastError() of the launch. prec is enum fdlbm_prec.
 cudaError_t launch_step_f64(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                             cudaStream_t s);
 cudaError_t launch_step_f32(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
@@ -121,6 +124,17 @@ cudaError_t launch_batch_f64(int variant, const BatchMember* mem, int nmem, long
 cudaError_t launch_batch_f32(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,
                              const Coeffs& c, cudaStream_t s);
 cudaError_t launch_gather_health(const BatchMember* mem, int nmem, unsigned* out, cudaStream_t s);
+// FDLBM_FNEQ32 (fdlbm_fneq.cu): the step, and the read-out / set-up kernels of that layout.
+cudaError_t launch_step_fneq(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
+                             cudaStream_t s);
+cudaError_t launch_init_fneq(void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
+                             const double* v, const double* T, cudaStream_t s);
+cudaError_t launch_dirichlet_fneq(void* f, const Grid& g, const double bstate[4][4], cudaStream_t s);
+cudaError_t launch_macro_fneq(const void* f, const Grid& g, double* rho, double* u, double* v, double* T,
+                              cudaStream_t s);
+cudaError_t launch_get_region_fneq(const void* f, const Grid& g, const Coeffs& c, int x0, int y0, int w, int h,
+                                   double* out, cudaStream_t s);
+cudaError_t launch_set_f_fneq(void* f, const Grid& g, const Coeffs& c, const double* in, cudaStream_t s);
 cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
                         unsigned* health, cudaStream_t s);
 cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
