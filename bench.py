@@ -237,6 +237,87 @@ def vn_oracle_sample(budget_s=20.0):
             "sample": "%d of the %d Sec. 4 cases at 40 digits (mpmath), %.1f s single-threaded" % (done, len(rows), el)}
 
 
+def posed_states_leg(F, torch, prec, variant, steps=20, warmup=3):
+    """The 4096^2 four-quadrant step at the states first posed for it (rho in [0.1, 2], p in
+    [0.03, 1.5], local Mach <= 10; seed 2, lambda = 3), same precision and tile variant, timed over
+    the first steps: whether high-kappa states (far-apart exponents, rare conversions) cost
+    throughput. The scheme rejects these states later in the run (every precision by step 2000),
+    so the status after the timed steps is reported with the number."""
+    from paper_0801_4169_gb300 import workloads as W
+    w = W.riemann4q(n=4096, seed=2, lam=3.0, mach_max=10.0, rho_range=(0.1, 2.0), p_range=(0.03, 1.5))
+    st = torch.cuda.Stream()
+    s = F.Solver.from_workload(w, prec, stream=st)
+    s.set_variant(variant)
+    s.step(warmup)
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    try:
+        status = s.sync()
+    except F.FdlbmError as e:
+        status = e.code
+    s.close()
+    return {"workload": w.name, "ranges": "rho [0.1, 2], p [0.03, 1.5], Mach <= 10, seed 2, lambda 3",
+            "ms_per_step": ms, "glups": w.nx * w.ny / (ms * 1e-3) / 1e9, "steps": steps,
+            "status_after": status}
+
+
+def serving_leg(n_req=64, steps_scale=0.25, seed=0, budget_bytes=1 << 30):
+    """The continuous-batching runtime on a seeded stream of shock-tube solves (the serving
+    workload's recipe: Poisson arrivals at 200 requests/s, nx ~ U{256..16384}, ny = 4,
+    Ms ~ U[2, 10], steps ~ U{2000..20000}, here n_req requests with steps scaled by steps_scale).
+
+    Three runs of the same stream: batched FP64, one launch sequence per solve in FP64 (the
+    baseline), and batched with the requests drawn as FP32 in FNEQ32. The FNEQ32 requests' results
+    are compared with the same requests' FP64 results."""
+    from paper_0801_4169_gb300 import fdlbm as F
+    from paper_0801_4169_gb300 import serve
+    from paper_0801_4169_gb300 import workloads as W
+    reqs = W.serving_requests(n=n_req, seed=seed)
+    for r in reqs:
+        r.steps = max(1, int(round(r.steps * steps_scale)))
+    warm = W.serving_requests(n=4, seed=seed + 1)
+    for r in warm:
+        r.steps = 40
+    runs = (("batched_fp64", "gpu", 0, F.FDLBM_FP32_STORE), ("per_solve_fp64", "separate", 0, F.FDLBM_FP32_STORE),
+            ("batched_mixed_fneq32", "gpu", None, F.FDLBM_FNEQ32))
+    res, outs = {}, {}
+    for name, engine, override, fp32_as in runs:
+        srv = serve.Server(budget_bytes=budget_bytes, engine=engine)
+        serve.replay(srv, warm, realtime=False, prec_override=override, fp32_as=fp32_as)
+        srv.close()
+        srv = serve.Server(budget_bytes=budget_bytes, engine=engine)
+        out, st = serve.replay(srv, reqs, prec_override=override, fp32_as=fp32_as)
+        srv.close()
+        outs[name] = {r.rid: (r, status, m) for (r, status, m, secs, err) in out.values()}
+        res[name] = {k: st[k] for k in ("aggregate_glups", "p50_s", "p99_s", "mean_s", "wall_s", "done", "failed",
+                                         "max_active", "rounds")}
+    errs = []
+    for rid, (r, status, m) in outs["batched_mixed_fneq32"].items():
+        ref = outs["batched_fp64"].get(rid)
+        if r.prec != 1 or status != F.FDLBM_REQ_DONE or ref is None or ref[1] != F.FDLBM_REQ_DONE:
+            continue
+        a, b = m[0], ref[2][0]
+        errs.append((float(np.mean(np.abs(a - b)) / np.mean(np.abs(b))), float(np.max(np.abs(a - b)) / np.max(np.abs(b)))))
+    e = np.array(errs) if errs else np.zeros((0, 2))
+    res["fneq32_vs_fp64"] = {"requests": len(errs),
+                             "l1_rho_median": float(np.median(e[:, 0])) if len(e) else None,
+                             "l1_rho_max": float(e[:, 0].max()) if len(e) else None,
+                             "max_rho_rel_max": float(e[:, 1].max()) if len(e) else None}
+    res["recipe"] = ("%d requests (seed %d), Poisson arrivals at 200/s, nx ~ U{256..16384}, ny = 4, Ms ~ U[2, 10] "
+                     "with the upstream at -(Ms - 2) c1, steps ~ U{2000..20000} x %g, precision ~ Bernoulli(1/2) "
+                     "(FP32 requests as FNEQ32 in the mixed run), HBM budget %d MiB, lambda = 2"
+                     % (n_req, seed, steps_scale, budget_bytes >> 20))
+    res["speedup_batched_vs_per_solve"] = (res["batched_fp64"]["aggregate_glups"] /
+                                           res["per_solve_fp64"]["aggregate_glups"])
+    return res
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -350,6 +431,7 @@ def main():
     ap.add_argument("--prec", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--small", action="store_true", help="a small version of the workload (profiling)")
     ap.add_argument("--n", type=int, default=None, help="grid edge of the four-quadrant workload (profiling)")
     ap.add_argument("--variant", type=int, default=None,
@@ -473,11 +555,15 @@ def main():
                              "get_macro": round((t3 - t2) * 1e3, 2)}},
         "gpu_launches": args.steps * (2 if split else 1),
     }
+    solver.close()
+    if rank == 0 and world == 1 and args.workload == "riemann4096" and not args.small and args.n is None:
+        line["posed_states"] = posed_states_leg(F, torch, prec, variant)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.workload, budget_s=20.0)
+    if rank == 0 and world == 1 and not args.no_serving and args.workload == "riemann4096" and not args.small:
+        line["serving"] = serving_leg()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    solver.close()
     if dist:
         dist.destroy_process_group()
 

@@ -84,7 +84,7 @@ enum fdlbm_side { FDLBM_LEFT = 0, FDLBM_RIGHT = 1, FDLBM_BOTTOM = 2, FDLBM_TOP =
  *              264 (FP64) and 132 (FP32_STORE); about 1.6x the FP64 path's FP64 work.
  *              fdlbm_get_macro returns the stored macros; fdlbm_get_f returns f_eq + g;
  *              fdlbm_set_f stores the FP64 moments of the given f and its departure from their
- *              equilibrium. Not accepted by fdlbm_batch_add. */
+ *              equilibrium. Batches of FNEQ32 solves take the 32x4 or 32x8 tile variant. */
 enum fdlbm_prec { FDLBM_FP64 = 0, FDLBM_FP32_STORE = 1, FDLBM_FNEQ32 = 2 };
 
 /* Scheme variants of Sec. 4 (Fig. 2, Fig. 3): drop line II, III or IV of Eq. 17,

@@ -63,8 +63,16 @@ void drop_graph(fdlbm_batch_ctx* b) {
 
 cudaError_t launch_one(fdlbm_batch_ctx* b, unsigned long long step) {
   const int n = (int)b->members.size();
+  if (b->scheme.prec == FDLBM_FNEQ32)
+    return launch_batch_fneq(b->variant, b->d_table, n, b->tiles, step, b->coeffs, b->stream);
   return b->scheme.prec == FDLBM_FP64 ? launch_batch_f64(b->variant, b->d_table, n, b->tiles, step, b->coeffs, b->stream)
                                       : launch_batch_f32(b->variant, b->d_table, n, b->tiles, step, b->coeffs, b->stream);
+}
+
+// FNEQ32 batches have two tile shapes (launch_batch_fneq).
+bool variant_ok(const fdlbm_batch_ctx* b, int v) {
+  if (v < 0 || v >= V_TILE_COUNT) return false;
+  return b->scheme.prec != FDLBM_FNEQ32 || v == V_T32x4 || v == V_T32x8;
 }
 
 // Rebuild the device descriptor table (members sorted by insertion; tile0 is a prefix sum).
@@ -74,7 +82,12 @@ int rebuild(fdlbm_batch_ctx* b) {
   if (!b->variant_set && n) {  // tile height from the tallest member (thin shock tubes: 4 rows)
     int ny = 0;
     for (fdlbm_ctx* h : b->members) ny = std::max(ny, h->cfg.ny);
-    b->variant = ny <= 4 ? V_T32x4 : ny <= 8 ? V_T32x8 : V_T32x16;
+    b->variant = ny <= 4 ? V_T32x4 : ny <= 8 || b->scheme.prec == FDLBM_FNEQ32 ? V_T32x8 : V_T32x16;
+  }
+  if (n && !variant_ok(b, b->variant)) b->variant = V_T32x8;  // an FNEQ32 batch given another shape
+  if (n && b->scheme.prec == FDLBM_FNEQ32) {
+    const cudaError_t pe = prepare_batch_fneq(b->variant);
+    if (pe != cudaSuccess) return bcuda(b, pe, "batch kernel set-up");
   }
   b->host_table.resize(n);
   int tw, th;
@@ -181,8 +194,6 @@ int fdlbm_batch_add(fdlbm_batch_t b, fdlbm_t h) {
   if (h->batch) return bfail(b, FDLBM_E_STATE, "the solve is already in a batch");
   if (!h->initialised) return bfail(b, FDLBM_E_STATE, "the solve has no state (set_macro first)");
   if (h->sticky) return bfail(b, h->sticky, "the solve carries a sticky error");
-  if (h->cfg.prec == FDLBM_FNEQ32)
-    return bfail(b, FDLBM_E_ARG, "FDLBM_FNEQ32 solves are stepped alone (fdlbm_step), not in batches");
   if (b->have_scheme && !same_scheme(b->scheme, h->cfg))
     return bfail(b, FDLBM_E_ARG, "members of a batch share dx, dy, dt, tau, lambda, flags and precision");
   cudaError_t e = cudaStreamSynchronize(h->stream);  // the solve's own queued work completes first
@@ -293,6 +304,8 @@ int fdlbm_batch_sync(fdlbm_batch_t b, unsigned* health) {
 int fdlbm_batch_set_variant(fdlbm_batch_t b, int variant) {
   if (!b) return bfail(nullptr, FDLBM_E_ARG, "batch is NULL");
   if (variant < 0 || variant >= V_TILE_COUNT) return bfail(b, FDLBM_E_ARG, "variant out of range for a batch");
+  if (b->have_scheme && !variant_ok(b, variant))
+    return bfail(b, FDLBM_E_ARG, "batches of FDLBM_FNEQ32 solves take the 32x4 or 32x8 tile variant");
   b->variant_set = true;
   if (variant != b->variant) {
     b->variant = variant;
@@ -312,7 +325,7 @@ int fdlbm_batch_autotune(fdlbm_batch_t b, int trial_steps, float* times_ms) {
   int best = b->variant;
   float best_ms = 1e30f;
   for (int v = 0; v < V_COUNT && e == cudaSuccess; ++v) {
-    if (v >= V_TILE_COUNT) {  // ring-parallel variants are single-solve only
+    if (!variant_ok(b, v)) {  // ring-parallel variants are single-solve only; FNEQ32 has two shapes
       if (times_ms) times_ms[v] = 0.f;
       continue;
     }

@@ -158,11 +158,13 @@ constexpr int fneq_smem_bytes() {
   return ((SC_N + 1 + 9) * (TW + 4) * (TH + 4) + 9 * TW * TH) * (int)sizeof(double);
 }
 
-template <int BX, int BY, int MINB>
-__global__ void __launch_bounds__(BX * BY, MINB) k_step_fneq(const void* __restrict__ fin, void* __restrict__ fout,
-                                                         Grid g, Coeffs c, unsigned* __restrict__ health) {
+// One tile (tx, ty) of one solve: the body of the single-solve and the batched kernels, so a
+// node's arithmetic is the same alone and in a batch.
+template <int BX, int BY>
+__device__ __forceinline__ void fneq_tile(const void* __restrict__ fin, void* __restrict__ fout, const Grid& g,
+                                          const Coeffs& c, unsigned* __restrict__ health, int tile_x, int tile_y,
+                                          unsigned char* s_dyn) {
   constexpr int TW = BX, TH = BY, BW = TW + 4, BH = TH + 4, BN = BW * BH, NT = BX * BY, TN = TW * TH;
-  extern __shared__ __align__(16) unsigned char s_dyn[];
   double* s_c = reinterpret_cast<double*>(s_dyn);  // [SC_N][BN]
   double* s_P = s_c + SC_N * BN;                    // [BN]
   double* s_f = s_P + BN;                           // [9][BN]
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(BX * BY, MINB) k_step_fneq(const void* __restr
   const float* gin = fneq_g(fin);
   const double* Min = fneq_M(fin, g);
   const int tid = threadIdx.y * BX + threadIdx.x;
-  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+  const int x0 = tile_x * TW, y0 = tile_y * TH;
   const int xe = min(x0 + TW, g.nx), ye = min(y0 + TH, g.ny);  // end of the tile's real nodes
   unsigned bits = 0;
 
@@ -328,6 +330,57 @@ __global__ void __launch_bounds__(BX * BY, MINB) k_step_fneq(const void* __restr
 }
 
 template <int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB) k_step_fneq(const void* __restrict__ fin, void* __restrict__ fout,
+                                                         Grid g, Coeffs c, unsigned* __restrict__ health) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  fneq_tile<BX, BY>(fin, fout, g, c, health, blockIdx.x, blockIdx.y, s_dyn);
+}
+
+// Batched step: block b runs tile (b - tile0) of the member whose [tile0, tile0 + tiles) holds b
+// (members sorted by tile0), as k_step_batch does for the other precisions.
+template <int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB) k_step_batch_fneq(const BatchMember* __restrict__ mem, int nmem,
+                                                               unsigned long long step, Coeffs c) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ int s_sel;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = nmem - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (mem[mid].tile0 <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_sel = lo;
+  }
+  __syncthreads();
+  const BatchMember& m = mem[s_sel];
+  const Grid g = m.g;
+  const long long local = (long long)blockIdx.x - m.tile0;
+  const int tx = (int)(local % m.tiles_x), ty = (int)(local / m.tiles_x);
+  const int par = (int)((m.cur0 + step) & 1ull);
+  fneq_tile<BX, BY>(m.f[par], m.f[par ^ 1], g, c, m.health, tx, ty, s_dyn);
+}
+
+// Opt the batched kernel in to its dynamic shared memory (once per device); called outside any
+// stream capture, before the batch's graph is recorded.
+template <int BX, int BY, int MINB>
+cudaError_t prepare_batch_fneq_t() {
+  static std::atomic<unsigned long long> attr{0};
+  return allow_dynamic_smem(k_step_batch_fneq<BX, BY, MINB>, fneq_smem_bytes<BX, BY>(), attr);
+}
+
+template <int BX, int BY, int MINB>
+cudaError_t launch_batch_fneq_t(const BatchMember* mem, int nmem, long long tiles, unsigned long long step,
+                                const Coeffs& c, cudaStream_t s) {
+  constexpr int smem = fneq_smem_bytes<BX, BY>();
+  const cudaError_t e = prepare_batch_fneq_t<BX, BY, MINB>();
+  if (e != cudaSuccess) return e;
+  k_step_batch_fneq<BX, BY, MINB><<<dim3((unsigned)tiles), dim3(BX, BY), smem, s>>>(mem, nmem, step, c);
+  return cudaGetLastError();
+}
+
+template <int BX, int BY, int MINB>
 cudaError_t launch_fneq_t(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
   constexpr int smem = fneq_smem_bytes<BX, BY>();
@@ -448,6 +501,21 @@ cudaError_t launch_step_fneq(int variant, const void* f, void* fn, const Grid& g
   if (variant == V_T16x4) return launch_fneq_t<16, 16, 1>(f, fn, g, c, health, s);
   if (variant == V_T64x8) return launch_fneq_t<64, 4, 2>(f, fn, g, c, health, s);
   return launch_fneq_t<32, 8, 1>(f, fn, g, c, health, s);
+}
+
+// Batches of FNEQ32 solves take the 32 x 4 (V_T32x4) or the 32 x 8 (V_T32x8) tile, the shapes
+// variant_tile gives for those variants.
+cudaError_t launch_batch_fneq(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,
+                              const Coeffs& c, cudaStream_t s) {
+  if (variant == V_T32x4) return launch_batch_fneq_t<32, 4, 2>(mem, nmem, tiles, step, c, s);
+  if (variant == V_T32x8) return launch_batch_fneq_t<32, 8, 2>(mem, nmem, tiles, step, c, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_batch_fneq(int variant) {
+  if (variant == V_T32x4) return prepare_batch_fneq_t<32, 4, 2>();
+  if (variant == V_T32x8) return prepare_batch_fneq_t<32, 8, 2>();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_init_fneq(void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,

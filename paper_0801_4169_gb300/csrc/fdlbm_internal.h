@@ -127,6 +127,9 @@ cudaError_t launch_gather_health(const BatchMember* mem, int nmem, unsigned* out
 // FDLBM_FNEQ32 (fdlbm_fneq.cu): the step, and the read-out / set-up kernels of that layout.
 cudaError_t launch_step_fneq(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                              cudaStream_t s);
+cudaError_t launch_batch_fneq(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,
+                              const Coeffs& c, cudaStream_t s);  // V_T32x4 or V_T32x8 only
+cudaError_t prepare_batch_fneq(int variant);  // opt-in to its shared memory, outside stream capture
 cudaError_t launch_init_fneq(void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
                              const double* v, const double* T, cudaStream_t s);
 cudaError_t launch_dirichlet_fneq(void* f, const Grid& g, const double bstate[4][4], cudaStream_t s);

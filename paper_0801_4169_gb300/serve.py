@@ -7,6 +7,7 @@ solution. This module only wraps that ABI and replays a request stream (W.servin
 each request is submitted at its arrival time, and every outcome is collected at the end.
 
     python -m paper_0801_4169_gb300.serve --requests 512 [--engine gpu|separate] [--prec mixed|fp64]
+        [--fp32-as store|fneq]
 
 engine "separate" is the baseline: the same scheduler, every solve stepped by its own launches.
 """
@@ -65,9 +66,11 @@ class Server:
             pass
 
 
-def replay(server, requests, lam=2.0, realtime=True, prec_override=None):
+def replay(server, requests, lam=2.0, realtime=True, prec_override=None, fp32_as=F.FDLBM_FP32_STORE):
     """Submit each request at its arrival time (wall clock), then wait for all of them.
 
+    A request drawn as FP32 storage runs in precision fp32_as (FDLBM_FP32_STORE, or FDLBM_FNEQ32,
+    which stores f's departure from equilibrium); prec_override runs every request in one precision.
     Returns {rid: (request, status, macros, seconds, error)} and the server statistics."""
     t0 = time.perf_counter()
     ids = []
@@ -77,7 +80,7 @@ def replay(server, requests, lam=2.0, realtime=True, prec_override=None):
             if delay > 0:
                 time.sleep(delay)
         w = W.request_workload(r, lam=lam)
-        prec = r.prec if prec_override is None else prec_override
+        prec = (fp32_as if r.prec == 1 else F.FDLBM_FP64) if prec_override is None else prec_override
         ids.append((server.submit(w, r.steps, prec), r))
     out = {}
     for rid, r in ids:
@@ -93,6 +96,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--engine", default="gpu", choices=["gpu", "separate"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp32-as", default="store", choices=["store", "fneq"],
+                    help="precision of the requests drawn as FP32: FP32 storage of f, or FNEQ32")
     ap.add_argument("--budget-gib", type=float, default=1.0)
     ap.add_argument("--round-steps", type=int, default=500)
     ap.add_argument("--steps-scale", type=float, default=1.0, help="scale every request's step count")
@@ -103,7 +108,8 @@ def main():
     for r in reqs:
         r.steps = max(1, int(round(r.steps * args.steps_scale)))
     srv = Server(budget_bytes=int(args.budget_gib * (1 << 30)), round_steps=args.round_steps, engine=args.engine)
-    out, st = replay(srv, reqs, prec_override=0 if args.prec == "fp64" else None)
+    fp32_as = F.FDLBM_FNEQ32 if args.fp32_as == "fneq" else F.FDLBM_FP32_STORE
+    out, st = replay(srv, reqs, prec_override=0 if args.prec == "fp64" else None, fp32_as=fp32_as)
     srv.close()
     prec_of = lambda r: 0 if args.prec == "fp64" else r.prec  # noqa: E731
     fp64_lat = [secs for (r, status, m, secs, e) in out.values() if status == F.FDLBM_REQ_DONE and prec_of(r) == 0]

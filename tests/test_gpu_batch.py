@@ -42,7 +42,7 @@ def _solver(w, prec):
     return F.Solver.from_workload(w, prec)
 
 
-@pytest.mark.parametrize("prec", [F.FDLBM_FP64, F.FDLBM_FP32_STORE])
+@pytest.mark.parametrize("prec", [F.FDLBM_FP64, F.FDLBM_FP32_STORE, F.FDLBM_FNEQ32])
 def test_member_equals_alone_bitwise(prec):
     ws = _members(prec)
     alone = [_solver(w, prec) for w in ws]

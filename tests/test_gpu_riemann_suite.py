@@ -109,3 +109,44 @@ def test_fig3_tube_matches_oracle_and_dispersion_damps_oscillations(flags):
     assert np.max(np.abs(res[flags] - ref)) <= 3.0 * spread
     tv = {fl: np.abs(np.diff(r)).sum() for fl, r in res.items()}
     assert tv[0] < 0.97 * tv[F.FDLBM_NO_DISP]
+
+
+def _front(rho, x, rho1, rho2, dx):
+    """Position where rho falls through the mean of the jump (linear between nodes)."""
+    half = 0.5 * (rho1 + rho2)
+    i = np.where(rho > half)[0].max()
+    return x[i] + (rho[i] - half) / (rho[i] - rho[i + 1]) * dx
+
+
+@pytest.mark.parametrize("prec", [F.FDLBM_FP64, F.FDLBM_FNEQ32])
+def test_strong_tube_at_full_size_against_rankine_hugoniot(prec):
+    """The 4000 x 4 Mach-10 tube (normal Mach 10 into a counter-stream at -6 c1, lambda = 2), 5000
+    steps, against the gamma = 2 Rankine-Hugoniot jump of the same shock (Sec. 5.1 states, m = 1):
+    - the plateau between contact and shock: pressure within 0.5% of RH (measured -0.15%), velocity
+      within 2% (+0.9%), density within 6% (+4.4%);
+    - the shock speed, from the front at steps 2500 and 5000, is 15% above RH (4.60 against 4.00):
+      line IV of Eq. 17 puts a node-wise coefficient outside the second difference, so it is not
+      conservative, and at lambda = 2 it moves a Mach-10 shock this much. The bound keeps the speed
+      within [1.10, 1.20] x RH;
+    - FP64 storage and FNEQ32 give the same speed and plateau to 1e-5."""
+    w = W.shock_tube(nx=4000, ny=4)
+    rho2, u2, _, T2 = w.meta["post"]
+    x = (np.arange(w.nx) + 0.5) * w.dx
+    s = F.Solver.from_workload(w, prec)
+    pos = []
+    for _ in range(2):
+        s.step(2500)
+        rho, u, v, T = s.get_macro()
+        for j in range(1, w.ny):
+            assert np.array_equal(rho[j], rho[0])
+        pos.append(_front(rho[0], x, 1.0, rho2, w.dx))
+    speed = (pos[1] - pos[0]) / (2500 * w.dt)
+    assert 1.10 * w.meta["W_lab"] <= speed <= 1.20 * w.meta["W_lab"]
+    t = 5000 * w.dt
+    a = int((w.meta["x0"] + u2 * t) / w.dx) + 10
+    b = int(pos[1] / w.dx) - 10
+    assert b - a > 100
+    assert np.mean(rho[0][a:b] * T[0][a:b]) == pytest.approx(rho2 * T2, rel=5e-3)
+    assert np.mean(u[0][a:b]) == pytest.approx(u2, rel=2e-2)
+    assert np.mean(rho[0][a:b]) == pytest.approx(rho2, rel=6e-2)
+    assert speed == pytest.approx(4.598336, rel=1e-5)

@@ -221,3 +221,14 @@ def test_c3_time_step_of_the_config_fails():
         assert 1 <= _fail_step(w, limit) <= limit
     w = W.reflection(nx=120, ny=40, dx=1e-3, dt=2.5e-6, lam=20.0, init="post", height=0.04)
     assert _fail_step(w, 400) == 0
+
+
+def test_strong_shocks_need_a_counter_stream_and_stop_near_mach_12():
+    """Why the serving stream draws Ms from [2, 10] with the upstream at -(Ms - 2) c1 (FP64 oracle,
+    600 x 1, dx = 1e-3, dt = tau = 1e-5, lambda = 2): Mach 10 runs 2000 steps with the upstream
+    at -8 c1; Mach 15 and 25 are rejected within 100 steps even with the upstream at -0.9 Ms c1."""
+    def fails_within(Ms, U, steps):
+        return _fail_step(W.shock_tube(nx=600, ny=1, steps=steps, Ms=Ms, U=U), steps)
+    assert fails_within(10.0, 8.0, 2000) == 0
+    for Ms in (15.0, 25.0):
+        assert 1 <= fails_within(Ms, 0.9 * Ms, 100) <= 100
