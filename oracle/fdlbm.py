@@ -46,6 +46,9 @@ def lib():
         L.orc_get_f_padded.argtypes = [ctypes.c_void_p, dp]
         L.orc_step.restype = ctypes.c_int
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+        L.orc_set_segment.restype = ctypes.c_int
+        L.orc_set_segment.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, dp]
         L.orc_steps_done.restype = ctypes.c_long
         L.orc_steps_done.argtypes = [ctypes.c_void_p]
         _lib = L
@@ -134,6 +137,15 @@ class Sim:
         f = np.zeros((Q, self.ny + 4, self.nx + 4))
         lib().orc_get_f_padded(self._h, _p(f))
         return f
+
+    def set_segment(self, side, c0, speed, lower, state):
+        """A Dirichlet segment on `side` (Sec. 5.2.2): the side's ghosts whose coordinate along it,
+        (i + 1/2) dx or (j + 1/2) dy, is below (lower) or at/above (not lower) c0 + speed * t hold
+        f_eq(state) at time t = steps * dt; the rest of the side keeps its kind. Set it before
+        set_macro / set_f."""
+        st = np.ascontiguousarray(state, dtype=np.float64)
+        if lib().orc_set_segment(self._h, int(side), float(c0), float(speed), int(bool(lower)), _p(st)):
+            raise ValueError("side out of range")
 
     def step(self, nsteps=1):
         """Advance nsteps; returns 0, or -4 if non-finite moments or P <= 0 appeared."""

@@ -173,6 +173,12 @@ typedef struct {
   double bstate[4][4];  /* Dirichlet (rho, u, v, T) per side */
   int flags;
   long steps_done;
+  /* Optional Dirichlet segment per side (Sec. 5.2.2, double Mach reflection): the ghosts of the
+   * side whose coordinate along it, (i + 1/2) dx or (j + 1/2) dy, lies below (lower = 1) or at or
+   * above (lower = 0) the split c0 + speed * t hold f_eq of seg_state at time t; the rest of the
+   * side follows its boundary kind. */
+  int seg_on[4], seg_lower[4];
+  double seg_c0[4], seg_speed[4], seg_state[4][4];
   int sx, sy;           /* padded extents nx+4, ny+4 */
   double* f;            /* [Q][sy][sx] */
   double* fn;
@@ -194,20 +200,36 @@ static int mirror_q(int q, int axis) {
 
 static int posmod(int a, int n) { return ((a % n) + n) % n; }
 
-/* Fill the ghost ring of buffer g: x-ghost columns on interior rows first,
+/* 1 if the ghost at along-side coordinate index a (node i or j) of `side` lies in the side's
+ * Dirichlet segment at time t. */
+static int in_segment(const orc_sim* s, int side, int a, double t) {
+  if (!s->seg_on[side]) return 0;
+  const double c = ((double)a + 0.5) * (side < 2 ? s->dy : s->dx);
+  const double split = s->seg_c0[side] + s->seg_speed[side] * t;
+  return s->seg_lower[side] ? (c < split) : !(c < split);
+}
+
+/* Fill the ghost ring of buffer g at time t: x-ghost columns on interior rows first,
  * then y-ghost rows across the full padded width. */
-static void fill_ghosts(orc_sim* s, double* g) {
+static void fill_ghosts(orc_sim* s, double* g, double t) {
   double vx[Q], vy[Q];
   orc_velocities(vx, vy);
   (void)vx; (void)vy;
-  double fe[4][Q];
-  for (int side = 0; side < 4; ++side)
+  double fe[4][Q], fseg[4][Q];
+  for (int side = 0; side < 4; ++side) {
     if (s->bc[side] == BC_DIRICHLET)
       orc_feq(s->bstate[side][0], s->bstate[side][1], s->bstate[side][2], s->bstate[side][3], fe[side]);
+    if (s->seg_on[side])
+      orc_feq(s->seg_state[side][0], s->seg_state[side][1], s->seg_state[side][2], s->seg_state[side][3], fseg[side]);
+  }
   int nx = s->nx, ny = s->ny;
 #define G(q, i, j) g[(size_t)(q) * s->sy * s->sx + (size_t)((j) + NG) * s->sx + (size_t)((i) + NG)]
   for (int j = 0; j < ny; ++j) {
     for (int gi = -NG; gi < 0; ++gi) { /* left */
+      if (in_segment(s, 0, j, t)) {
+        for (int q = 0; q < Q; ++q) G(q, gi, j) = fseg[0][q];
+        continue;
+      }
       for (int q = 0; q < Q; ++q) {
         switch (s->bc[0]) {
           case BC_PERIODIC: G(q, gi, j) = G(q, posmod(gi, nx), j); break;
@@ -218,6 +240,10 @@ static void fill_ghosts(orc_sim* s, double* g) {
       }
     }
     for (int gi = nx; gi < nx + NG; ++gi) { /* right */
+      if (in_segment(s, 1, j, t)) {
+        for (int q = 0; q < Q; ++q) G(q, gi, j) = fseg[1][q];
+        continue;
+      }
       for (int q = 0; q < Q; ++q) {
         switch (s->bc[1]) {
           case BC_PERIODIC: G(q, gi, j) = G(q, posmod(gi, nx), j); break;
@@ -230,6 +256,10 @@ static void fill_ghosts(orc_sim* s, double* g) {
   }
   for (int i = -NG; i < nx + NG; ++i) {
     for (int gj = -NG; gj < 0; ++gj) { /* bottom */
+      if (in_segment(s, 2, i, t)) {
+        for (int q = 0; q < Q; ++q) G(q, i, gj) = fseg[2][q];
+        continue;
+      }
       for (int q = 0; q < Q; ++q) {
         switch (s->bc[2]) {
           case BC_PERIODIC: G(q, i, gj) = G(q, i, posmod(gj, ny)); break;
@@ -240,6 +270,10 @@ static void fill_ghosts(orc_sim* s, double* g) {
       }
     }
     for (int gj = ny; gj < ny + NG; ++gj) { /* top */
+      if (in_segment(s, 3, i, t)) {
+        for (int q = 0; q < Q; ++q) G(q, i, gj) = fseg[3][q];
+        continue;
+      }
       for (int q = 0; q < Q; ++q) {
         switch (s->bc[3]) {
           case BC_PERIODIC: G(q, i, gj) = G(q, i, posmod(gj, ny)); break;
@@ -294,8 +328,19 @@ void orc_set_macro(orc_sim* s, const double* rho, const double* u, const double*
       orc_feq(rho[m], u[m], v[m], T[m], fe);
       for (int q = 0; q < Q; ++q) s->f[FI(s, q, i, j)] = fe[q];
     }
-  fill_ghosts(s, s->f);
   s->steps_done = 0;
+  fill_ghosts(s, s->f, 0.0);
+}
+
+/* A Dirichlet segment on `side` (see orc_sim); takes effect at the next ghost fill. */
+int orc_set_segment(orc_sim* s, int side, double c0, double speed, int lower, const double* state) {
+  if (side < 0 || side > 3) return -1;
+  s->seg_on[side] = 1;
+  s->seg_c0[side] = c0;
+  s->seg_speed[side] = speed;
+  s->seg_lower[side] = lower ? 1 : 0;
+  for (int a = 0; a < 4; ++a) s->seg_state[side][a] = state[a];
+  return 0;
 }
 
 /* raw f access, interior only, layout [q][j][i] (for perturbation tests) */
@@ -304,7 +349,7 @@ void orc_set_f(orc_sim* s, const double* f) {
     for (int j = 0; j < s->ny; ++j)
       for (int i = 0; i < s->nx; ++i)
         s->f[FI(s, q, i, j)] = f[((size_t)q * s->ny + j) * s->nx + i];
-  fill_ghosts(s, s->f);
+  fill_ghosts(s, s->f, (double)s->steps_done * s->dt);
 }
 
 void orc_get_f(const orc_sim* s, double* f) {
@@ -391,8 +436,8 @@ static int step_once(orc_sim* s) {
         s->fn[FI(s, q, i, j)] = acc;
       }
     }
-  /* (5) ghost ring of the new field, then swap */
-  fill_ghosts(s, s->fn);
+  /* (5) ghost ring of the new field (at time (steps + 1) dt), then swap */
+  fill_ghosts(s, s->fn, (double)(s->steps_done + 1) * s->dt);
   double* t = s->f;
   s->f = s->fn;
   s->fn = t;
