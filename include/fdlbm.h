@@ -134,6 +134,22 @@ int fdlbm_create(fdlbm_t* out, int nx, int ny, double dx, double dy, double dt, 
  * ghosts become f_eq of that state (Eq. 10). Enqueued on the stream. */
 int fdlbm_set_boundary_state(fdlbm_t h, int side, double rho, double u, double v, double T);
 
+/* A Dirichlet segment on one side, for boundaries that change along a side or in time (the
+ * double Mach reflection of Sec. 5.2.2: the post-shock state on the bottom before the wall starts
+ * at x = 0.08, and on the top left of the moving shock, x <= g(t)). The paper gives no mechanics;
+ * this one is a reading. At time t = steps * dt, the side's ghosts (both layers, at the interior's
+ * columns or rows) whose coordinate along the side, (i + 1/2) dx for bottom/top or (j + 1/2) dy
+ * for left/right, lies below the split c0 + speed * t (lower != 0), or at or above it (lower == 0),
+ * hold f_eq of (rho, u, v, T). The rest of the side keeps its kind: a DIRICHLET side its own
+ * state, a WALL or OUTFLOW side the ghost copies its interior nodes write. One segment per side;
+ * a new call replaces it. fdlbm_step applies it after every step, with the time of the new state.
+ * FDLBM_E_ARG for a periodic side, a non-finite c0 or speed, or a state without rho > 0, T > 0.
+ * Solves with segments are stepped alone: fdlbm_batch_add refuses them, and fdlbm_step_noalloc
+ * (which takes no handle) knows nothing of them. */
+int fdlbm_set_boundary_segment(fdlbm_t h, int side, double c0, double speed, int lower, double rho, double u,
+                               double v, double T);
+int fdlbm_clear_boundary_segment(fdlbm_t h, int side);
+
 /* Initial condition: f = f_eq(rho, u, v, T) at every node (Eq. 10), ghost ring
  * filled per boundary kind. Host arrays of nx*ny doubles; copied before
  * return. Resets the step count and clears a sticky error. */

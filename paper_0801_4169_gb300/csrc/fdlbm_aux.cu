@@ -4,6 +4,51 @@
 
 namespace fdlbm {
 
+namespace {
+
+// Ghost node t of a side's two layers next to the interior (t < 2 len, len = ny for left/right,
+// nx for top/bottom): its coordinates and its index along the side.
+__device__ __forceinline__ void side_ghost(const Grid& g, int side, int t, int& gx, int& gy, int& along) {
+  const int len = side < 2 ? g.ny : g.nx;
+  along = t % len;
+  const int layer = t / len;  // 0: next to the interior, 1: outer
+  if (side == 0) { gx = -1 - layer; gy = along; }
+  else if (side == 1) { gx = g.nx + layer; gy = along; }
+  else if (side == 2) { gx = along; gy = -1 - layer; }
+  else { gx = along; gy = g.ny + layer; }
+}
+
+template <typename S>
+__global__ void k_segment(S* __restrict__ f, Grid g, Coeffs c, Segment sg, double d) {
+  const int len = sg.side < 2 ? g.ny : g.nx;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * len) return;
+  int gx, gy, along;
+  side_ghost(g, sg.side, t, gx, gy, along);
+  const double pos = ((double)along + 0.5) * d;
+  const bool in = sg.lower ? (pos < sg.split) : !(pos < sg.split);
+  if (!in && !sg.base_dirichlet) return;
+  const double* st = in ? sg.seg : sg.base;
+  GhostOwn none;
+  none.mx = 0;
+  none.my = 0;
+  write_feq<S>(f, g, c, gx, gy, none, st[0], st[1], st[2], st[3]);
+}
+
+}  // namespace
+
+cudaError_t launch_segment(int prec, void* f, const Grid& g, const Coeffs& c, const Segment& sg, double dx, double dy,
+                           cudaStream_t s) {
+  const int len = sg.side < 2 ? g.ny : g.nx;
+  const double d = sg.side < 2 ? dy : dx;
+  dim3 b(128), grid((2 * len + 127) / 128);
+  if (prec == 0)
+    k_segment<double><<<grid, b, 0, s>>>(static_cast<double*>(f), g, c, sg, d);
+  else
+    k_segment<float><<<grid, b, 0, s>>>(static_cast<float*>(f), g, c, sg, d);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
                         unsigned* health, cudaStream_t s) {
   if (prec == FDLBM_FNEQ32) return launch_step_fneq(variant, f, fn, g, c, health, s);

@@ -193,12 +193,40 @@ int enqueue_health_copy(fdlbm_ctx* h) {
   return FDLBM_OK;
 }
 
-int fill_ghosts_dirichlet(fdlbm_ctx* h) {
+bool any_segment(const fdlbm_ctx* h) { return h->seg_on[0] || h->seg_on[1] || h->seg_on[2] || h->seg_on[3]; }
+
+// The Dirichlet segments of every side at the time of step `steps_at` (t = steps_at * dt), in
+// buffer buf.
+int apply_segments(fdlbm_ctx* h, void* buf, long steps_at) {
+  const double t = (double)steps_at * h->cfg.dt;
+  for (int side = 0; side < 4; ++side) {
+    if (!h->seg_on[side]) continue;
+    Segment sg;
+    sg.side = side;
+    sg.lower = h->seg_lower[side];
+    sg.base_dirichlet = h->cfg.bc[side] == FDLBM_BC_DIRICHLET;
+    sg.split = h->seg_c0[side] + h->seg_speed[side] * t;
+    for (int a = 0; a < 4; ++a) {
+      sg.seg[a] = h->seg_state[side][a];
+      sg.base[a] = h->bstate[side][a];
+    }
+    cudaError_t e = h->cfg.prec == FDLBM_FNEQ32
+                        ? launch_segment_fneq(buf, h->grid, sg, h->cfg.dx, h->cfg.dy, h->stream)
+                        : launch_segment(h->cfg.prec, buf, h->grid, h->coeffs, sg, h->cfg.dx, h->cfg.dy, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "segment launch");
+  }
+  return FDLBM_OK;
+}
+
+// Dirichlet ghosts of both buffers (and the segments, at the time of step steps_at).
+int fill_ghosts_dirichlet(fdlbm_ctx* h, long steps_at) {
   for (int b = 0; b < 2; ++b) {
     cudaError_t e = h->cfg.prec == FDLBM_FNEQ32 ? launch_dirichlet_fneq(h->f[b], h->grid, h->bstate, h->stream)
                                                 : launch_dirichlet(h->cfg.prec, h->f[b], h->grid, h->coeffs, h->bstate,
                                                                    h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "dirichlet launch");
+    int rc = apply_segments(h, h->f[b], steps_at);
+    if (rc) return rc;
   }
   return FDLBM_OK;
 }
@@ -213,7 +241,7 @@ int init_from_device_macros(fdlbm_ctx* h, const double* rho, const double* u, co
                                     : launch_init(h->cfg.prec, h->f[b], h->grid, h->coeffs, rho, u, v, T, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "init launch");
   }
-  int rc = fill_ghosts_dirichlet(h);
+  int rc = fill_ghosts_dirichlet(h, 0);
   if (rc) return rc;
   h->cur = 0;
   h->steps = 0;
@@ -346,7 +374,35 @@ int fdlbm_set_boundary_state(fdlbm_t h, int side, double rho, double u, double v
   h->bstate[side][1] = u;
   h->bstate[side][2] = v;
   h->bstate[side][3] = T;
-  if (h->cfg.bc[side] == FDLBM_BC_DIRICHLET && h->initialised) return fill_ghosts_dirichlet(h);
+  if (h->cfg.bc[side] == FDLBM_BC_DIRICHLET && h->initialised) return fill_ghosts_dirichlet(h, h->steps);
+  return FDLBM_OK;
+}
+
+int fdlbm_set_boundary_segment(fdlbm_t h, int side, double c0, double speed, int lower, double rho, double u,
+                               double v, double T) {
+  if (h && h->batch) return fail(h, FDLBM_E_STATE, "the solve is a member of a batch (remove it first)");
+  if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
+  if (side < 0 || side > 3) return fail(h, FDLBM_E_ARG, "side out of range");
+  if (h->cfg.bc[side] == FDLBM_BC_PERIODIC) return fail(h, FDLBM_E_ARG, "a periodic side takes no segment");
+  if (!std::isfinite(c0) || !std::isfinite(speed)) return fail(h, FDLBM_E_ARG, "c0 and speed must be finite");
+  if (!(rho > 0) || !(T > 0) || !std::isfinite(u) || !std::isfinite(v) || !std::isfinite(rho) || !std::isfinite(T))
+    return fail(h, FDLBM_E_ARG, "segment state needs finite rho > 0, T > 0");
+  h->seg_on[side] = true;
+  h->seg_lower[side] = lower ? 1 : 0;
+  h->seg_c0[side] = c0;
+  h->seg_speed[side] = speed;
+  h->seg_state[side][0] = rho;
+  h->seg_state[side][1] = u;
+  h->seg_state[side][2] = v;
+  h->seg_state[side][3] = T;
+  if (h->initialised) return fill_ghosts_dirichlet(h, h->steps);
+  return FDLBM_OK;
+}
+
+int fdlbm_clear_boundary_segment(fdlbm_t h, int side) {
+  if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
+  if (side < 0 || side > 3) return fail(h, FDLBM_E_ARG, "side out of range");
+  h->seg_on[side] = false;
   return FDLBM_OK;
 }
 
@@ -388,6 +444,10 @@ int fdlbm_step(fdlbm_t h, long nsteps) {
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     h->cur = 1 - h->cur;
     h->steps += 1;
+    if (any_segment(h)) {
+      const int rc = apply_segments(h, h->f[h->cur], h->steps);
+      if (rc) return rc;
+    }
   }
   // health bits accumulate on the device, so a newer copy supersedes a pending one
   if (nsteps > 0) return enqueue_health_copy(h);
@@ -502,7 +562,7 @@ int fdlbm_set_f(fdlbm_t h, const double* f) {
                                     : launch_set_f(h->cfg.prec, h->f[b], h->grid, h->d_fstage, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_f launch");
   }
-  rc = fill_ghosts_dirichlet(h);
+  rc = fill_ghosts_dirichlet(h, h->steps);
   if (rc) return rc;
   e = cudaMemsetAsync(h->d_health, 0, sizeof(unsigned), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -432,6 +432,30 @@ __global__ void k_dirichlet_fneq(void* f, Grid g, BState bs) {
   store_macros(st.M, g, gx, gy, none, bs.s[side][0], bs.s[side][1], bs.s[side][2], bs.s[side][3]);
 }
 
+// A side's Dirichlet segment (see launch_segment): the state's macros with g = 0.
+__global__ void k_segment_fneq(void* f, Grid g, Segment sg, double d) {
+  const int len = sg.side < 2 ? g.ny : g.nx;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * len) return;
+  const int along = t % len, layer = t / len;
+  int gx, gy;
+  if (sg.side == 0) { gx = -1 - layer; gy = along; }
+  else if (sg.side == 1) { gx = g.nx + layer; gy = along; }
+  else if (sg.side == 2) { gx = along; gy = -1 - layer; }
+  else { gx = along; gy = g.ny + layer; }
+  const double pos = ((double)along + 0.5) * d;
+  const bool in = sg.lower ? (pos < sg.split) : !(pos < sg.split);
+  if (!in && !sg.base_dirichlet) return;
+  const double* st = in ? sg.seg : sg.base;
+  GhostOwn none;
+  none.mx = 0;
+  none.my = 0;
+  FneqState s = fneq_state(f, g);
+  const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
+  for (int q = 0; q < Q; ++q) s.g[(long long)q * g.plane + off] = 0.0f;
+  store_macros(s.M, g, gx, gy, none, st[0], st[1], st[2], st[3]);
+}
+
 __global__ void k_macro_fneq(const void* f, Grid g, double* __restrict__ rho, double* __restrict__ u,
                              double* __restrict__ v, double* __restrict__ T) {
   const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
@@ -533,6 +557,13 @@ cudaError_t launch_dirichlet_fneq(void* f, const Grid& g, const double bstate[4]
   const int len = 2 * (g.nx > g.ny ? g.nx : g.ny);
   dim3 b(128), grid((len + 127) / 128, 4);
   k_dirichlet_fneq<<<grid, b, 0, s>>>(f, g, bs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segment_fneq(void* f, const Grid& g, const Segment& sg, double dx, double dy, cudaStream_t s) {
+  const int len = sg.side < 2 ? g.ny : g.nx;
+  dim3 b(128), grid((2 * len + 127) / 128);
+  k_segment_fneq<<<grid, b, 0, s>>>(f, g, sg, sg.side < 2 ? dy : dx);
   return cudaGetLastError();
 }
 

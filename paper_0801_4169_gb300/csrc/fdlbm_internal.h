@@ -150,6 +150,17 @@ cudaError_t launch_get_f(int prec, const void* f, const Grid& g, double* out, cu
 cudaError_t launch_get_region(int prec, const void* f, const Grid& g, int x0, int y0, int w, int h, double* out,
                               cudaStream_t s);
 cudaError_t launch_set_f(int prec, void* f, const Grid& g, const double* in, cudaStream_t s);
+// A side's Dirichlet segment at one time (fdlbm_set_boundary_segment): the ghosts of `side` whose
+// coordinate along it lies below (lower) or at/above `split` get f_eq of seg; with base_dirichlet
+// the others get f_eq of base (the side's own Dirichlet state).
+struct Segment {
+  int side, lower, base_dirichlet;
+  double split;
+  double seg[4], base[4];
+};
+cudaError_t launch_segment(int prec, void* f, const Grid& g, const Coeffs& c, const Segment& sg, double dx, double dy,
+                           cudaStream_t s);
+cudaError_t launch_segment_fneq(void* f, const Grid& g, const Segment& sg, double dx, double dy, cudaStream_t s);
 
 // Host helpers shared by the C ABI files (fdlbm_capi.cu).
 struct Layout {
@@ -191,6 +202,10 @@ struct fdlbm_ctx {
   unsigned health = 0;
   int variant = fdlbm::V_T32x8;
   double bstate[4][4];
+  // Dirichlet segments per side (fdlbm_set_boundary_segment)
+  bool seg_on[4] = {false, false, false, false};
+  int seg_lower[4] = {0, 0, 0, 0};
+  double seg_c0[4] = {0, 0, 0, 0}, seg_speed[4] = {0, 0, 0, 0}, seg_state[4][4] = {};
   std::string err;
   struct fdlbm_batch_ctx* batch = nullptr;  // the batch this solve is a member of, if any
 };

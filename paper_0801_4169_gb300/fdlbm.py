@@ -76,6 +76,9 @@ def lib():
         sig = {
             "fdlbm_device_bytes": (ctypes.c_size_t, [cfgp]),
             "fdlbm_create_ex": (ctypes.c_int, [ctypes.POINTER(_VP), cfgp, _VP, ctypes.c_size_t, _VP]),
+            "fdlbm_set_boundary_segment": (ctypes.c_int, [_VP, ctypes.c_int] + [ctypes.c_double] * 2 +
+                                           [ctypes.c_int] + [ctypes.c_double] * 4),
+            "fdlbm_clear_boundary_segment": (ctypes.c_int, [_VP, ctypes.c_int]),
             "fdlbm_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 +
                              [ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
             "fdlbm_set_boundary_state": (ctypes.c_int, [_VP, ctypes.c_int] + [ctypes.c_double] * 4),
@@ -197,6 +200,15 @@ def fdlbm_create(nx, ny, dx, dy, dt, tau, lam, bc, prec=FDLBM_FP64, stream=None)
 
 def fdlbm_set_boundary_state(h, side, rho, u, v, T):
     return _check(h, lib().fdlbm_set_boundary_state(h, int(side), rho, u, v, T))
+
+
+def fdlbm_set_boundary_segment(h, side, c0, speed, lower, rho, u, v, T):
+    return _check(h, lib().fdlbm_set_boundary_segment(h, int(side), float(c0), float(speed), int(bool(lower)),
+                                                       float(rho), float(u), float(v), float(T)))
+
+
+def fdlbm_clear_boundary_segment(h, side):
+    return _check(h, lib().fdlbm_clear_boundary_segment(h, int(side)))
 
 
 def fdlbm_set_macro(h, rho, u, v, T, n=None):
@@ -514,6 +526,8 @@ class Solver:
     @classmethod
     def from_workload(cls, w, prec=FDLBM_FP64, flags=0, stream=None, use_torch_memory=True):
         s = cls(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, prec, flags, w.bstate, stream, use_torch_memory)
+        for side, c0, speed, lower, st in w.meta.get("segments", ()):
+            fdlbm_set_boundary_segment(s.h, side, c0, speed, lower, *st)
         s.set_macro(*w.macros())
         return s
 

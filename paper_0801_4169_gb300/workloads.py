@@ -21,13 +21,15 @@ Workloads (all FP64 macros, x fastest, m = 1 so rho = n and p = rho*T):
                 -5.71578, 22.61); Dirichlet left and top, outflow right, specular
                 wall at the bottom; lambda = 20, dt = tau = 0.0025 dx. The paper gives no initial field;
                 the domain starts in the top state and the incident shock forms at
-                the top-left corner (a sharp initial 30-degree shock is rejected by
-                the scheme within a few steps for every lambda tried).
+                the top-left corner (init="shock" starts from a sharp 30-degree shock, which
+                the scheme rejects within a few steps for lambda = 1 and 5 but runs at 20).
   riemann4q     four-quadrant 2-D Riemann problem with seeded quadrant states,
                 outflow on every side.
   serving_requests  seeded Poisson stream of shock-tube solves of mixed size,
                 Mach number, length and precision.
   riemann1d     the 1-D Riemann problems of Sec. 5.1 (Eqs. 21-25) on ny = 1.
+  dmr           double Mach reflection of Sec. 5.2.2 (Eq. 27): 60-degree shock into gas at rest,
+                wall from x = 0.08, a moving Dirichlet segment on the top boundary.
   vn_sec4       the von Neumann sweeps of Sec. 4 (Figs. 2, 4, 5, 6): uniform states,
                 lambda and scheme variants, each over nk wave numbers k dx in (0, pi].
 """
@@ -175,6 +177,43 @@ def riemann4q(n=4096, seed=0, steps=2000, dx=2.5e-4, dt=2.5e-6, tau=2.5e-6, lam=
     rho, u, v, T = _fields(nx, ny, [arr[quad, i] for i in range(4)])
     return Workload("riemann4q%dx%d_s%d" % (nx, ny, seed), nx, ny, dx, dx, dt, tau, lam,
                     (OUTFLOW,) * 4, steps, rho, u, v, T, meta=dict(states=states, seed=seed))
+
+
+DMR_PRE = (2.0, 0.0, 0.0, 0.5)  # Eq. 27, gas ahead of the shock (sound speed 1)
+
+
+def dmr(Ms=20.0, nx=500, ny=200, dx=1e-3, dt=1e-5, tau=None, lam=20.0, steps=750, x_wall=0.08):
+    """Double Mach reflection (Sec. 5.2.2, Eq. 27) on an nx x ny grid of spacing dx.
+
+    A planar shock of normal Mach Ms runs into gas at rest (2, 0, 0, 0.5) at 60 degrees to the x axis;
+    behind it the gamma = 2 Rankine-Hugoniot state (400/67, 13.3, 89.2775 at Ms = 20) moves along the
+    shock normal (cos 30, -sin 30). The shock line is y = h(x, t) = sqrt(3) (x - x_wall) - 2 W t
+    (W = Ms c1, so 2W = 40 at Ms = 20), post-shock gas above it. Boundaries: Dirichlet post-shock
+    state on the left; outflow on the right; at the bottom a specular wall from x = x_wall on, the
+    post-shock state before it; at the top the post-shock state for x below
+    g(t) = x_wall + (H + 2 W t)/sqrt(3) (H the domain height) and the gas at rest beyond. The two
+    segments are returned in meta["segments"] as (side, c0, speed, lower, state). The scheme
+    rejects Ms = 20 (the Eq. 27 data) in exact arithmetic; the default Ms is the paper's."""
+    if tau is None:
+        tau = dt
+    rho1, u1, v1, T1 = DMR_PRE
+    rho2, un, T2, W = rh_moving_shock(Ms, rho1, T1)
+    c30, s30 = math.cos(math.radians(30.0)), math.sin(math.radians(30.0))
+    post = (rho2, un * c30, -un * s30, T2)
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dx
+    X, Y = np.meshgrid(x, y)
+    behind = Y >= math.sqrt(3.0) * (X - x_wall)
+    rho, u, v, T = _fields(nx, ny, [np.where(behind, post[i], DMR_PRE[i]) for i in range(4)])
+    H = ny * dx
+    bstate = np.zeros((4, 4))
+    bstate[0] = post   # left: Dirichlet post-shock
+    bstate[3] = DMR_PRE  # top beyond the moving segment
+    segments = [(2, x_wall, 0.0, True, post),                                   # bottom, before the wall
+                (3, x_wall + H / math.sqrt(3.0), 2.0 * W / math.sqrt(3.0), True, post)]  # top, moving
+    return Workload("dmr%gx%dx%d" % (Ms, nx, ny), nx, ny, dx, dx, dt, tau, lam,
+                    (DIRICHLET, OUTFLOW, WALL, DIRICHLET), steps, rho, u, v, T, bstate=bstate,
+                    meta=dict(pre=DMR_PRE, post=post, W=W, x_wall=x_wall, segments=segments, Ms=Ms))
 
 
 RIEMANN1D = {
