@@ -15,8 +15,9 @@ from . import build as _build
 
 Q = 33
 
-# boundary kinds (left, right, bottom, top)
-PERIODIC, OUTFLOW, DIRICHLET, WALL = 0, 1, 2, 3
+# boundary kinds (left, right, bottom, top); HALO: ghosts written by the caller (a neighbouring
+# sub-domain), never by the oracle's fill
+PERIODIC, OUTFLOW, DIRICHLET, WALL, HALO = 0, 1, 2, 3, 4
 
 # Eq. 17 variants (Sec. 4): drop line II, III, IV, or hold the switch at lambda
 NO_LW, NO_DISP, NO_VISC, SWITCH_CONST = 1, 2, 4, 8
@@ -44,6 +45,7 @@ def lib():
         L.orc_set_f.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_f.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_f_padded.argtypes = [ctypes.c_void_p, dp]
+        L.orc_set_f_padded.argtypes = [ctypes.c_void_p, dp]
         L.orc_step.restype = ctypes.c_int
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
         L.orc_set_segment.restype = ctypes.c_int
@@ -146,6 +148,11 @@ class Sim:
         st = np.ascontiguousarray(state, dtype=np.float64)
         if lib().orc_set_segment(self._h, int(side), float(c0), float(speed), int(bool(lower)), _p(st)):
             raise ValueError("side out of range")
+
+    def set_f_padded(self, f):
+        """Write the whole padded buffer, ghosts included, as given (no ghost fill)."""
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(Q, self.ny + 4, self.nx + 4)
+        lib().orc_set_f_padded(self._h, _p(f))
 
     def step(self, nsteps=1):
         """Advance nsteps; returns 0, or -4 if non-finite moments or P <= 0 appeared."""

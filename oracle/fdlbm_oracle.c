@@ -54,6 +54,7 @@
 #define BC_OUTFLOW 1
 #define BC_DIRICHLET 2
 #define BC_WALL 3
+#define BC_HALO 4 /* ghosts written by the caller (a neighbouring sub-domain), never by the fill */
 
 /* ---------------------------------------------------------------------- */
 /* Sec. 2, Eq. 1: v_0 = 0; v_ki = v_k (cos(i pi/4), sin(i pi/4)), i = 1..8.  */
@@ -225,7 +226,7 @@ static void fill_ghosts(orc_sim* s, double* g, double t) {
   int nx = s->nx, ny = s->ny;
 #define G(q, i, j) g[(size_t)(q) * s->sy * s->sx + (size_t)((j) + NG) * s->sx + (size_t)((i) + NG)]
   for (int j = 0; j < ny; ++j) {
-    for (int gi = -NG; gi < 0; ++gi) { /* left */
+    for (int gi = -NG; gi < 0 && s->bc[0] != BC_HALO; ++gi) { /* left */
       if (in_segment(s, 0, j, t)) {
         for (int q = 0; q < Q; ++q) G(q, gi, j) = fseg[0][q];
         continue;
@@ -239,7 +240,7 @@ static void fill_ghosts(orc_sim* s, double* g, double t) {
         }
       }
     }
-    for (int gi = nx; gi < nx + NG; ++gi) { /* right */
+    for (int gi = nx; gi < nx + NG && s->bc[1] != BC_HALO; ++gi) { /* right */
       if (in_segment(s, 1, j, t)) {
         for (int q = 0; q < Q; ++q) G(q, gi, j) = fseg[1][q];
         continue;
@@ -255,7 +256,7 @@ static void fill_ghosts(orc_sim* s, double* g, double t) {
     }
   }
   for (int i = -NG; i < nx + NG; ++i) {
-    for (int gj = -NG; gj < 0; ++gj) { /* bottom */
+    for (int gj = -NG; gj < 0 && s->bc[2] != BC_HALO; ++gj) { /* bottom */
       if (in_segment(s, 2, i, t)) {
         for (int q = 0; q < Q; ++q) G(q, i, gj) = fseg[2][q];
         continue;
@@ -269,7 +270,7 @@ static void fill_ghosts(orc_sim* s, double* g, double t) {
         }
       }
     }
-    for (int gj = ny; gj < ny + NG; ++gj) { /* top */
+    for (int gj = ny; gj < ny + NG && s->bc[3] != BC_HALO; ++gj) { /* top */
       if (in_segment(s, 3, i, t)) {
         for (int q = 0; q < Q; ++q) G(q, i, gj) = fseg[3][q];
         continue;
@@ -291,7 +292,7 @@ orc_sim* orc_create(int nx, int ny, double dx, double dy, double dt, double tau,
                     const int* bc, const double* bstate /* 4x4 */, int flags) {
   if (nx < 1 || ny < 1) return NULL;
   for (int side = 0; side < 4; ++side) {
-    if (bc[side] < 0 || bc[side] > 3) return NULL;
+    if (bc[side] < 0 || bc[side] > 4) return NULL;
     if (bc[side] == BC_WALL && ((side < 2 && nx < 2) || (side >= 2 && ny < 2))) return NULL;
   }
   if ((bc[0] == BC_PERIODIC) != (bc[1] == BC_PERIODIC)) return NULL;
@@ -357,6 +358,12 @@ void orc_get_f(const orc_sim* s, double* f) {
     for (int j = 0; j < s->ny; ++j)
       for (int i = 0; i < s->nx; ++i)
         f[((size_t)q * s->ny + j) * s->nx + i] = s->f[FI(s, q, i, j)];
+}
+
+/* full padded buffer (ghosts included), layout [q][j+2][i+2], written as given (no ghost fill):
+ * a sub-domain's halo rows come from its neighbour */
+void orc_set_f_padded(orc_sim* s, const double* f) {
+  memcpy(s->f, f, (size_t)Q * s->sx * s->sy * sizeof(double));
 }
 
 /* full padded buffer (ghosts included), layout [q][j+2][i+2] */
