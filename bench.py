@@ -45,8 +45,9 @@ sys.path.insert(0, ROOT)
 # once: ncu thread-level counts of the split step's two kernels, whose sum is the fused step's
 # work without the moments of the tile ring (see profiles/). FP32 storage sums its moments in
 # 64-bit fixed point on the integer pipes, hence the lower count (FP32 storage: 130 update +
-# 15 moments; FP64: 481 + 89).
-FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145}
+# 15 moments; FP64: 481 + 89). FNEQ32: ncu's count of k_step_fneq per site (the equilibrium rebuilt
+# on each tile's halo before the stencil and formed again from the new moments).
+FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145, "fneq32": 927}
 # DRAM bytes (read + write) per site update of one step's launches (k_step, or k_moments +
 # k_update), by (precision, tile variant): ncu dram__bytes_read.sum + dram__bytes_write.sum of one
 # step of this bench's 4096^2 workload (single-pass capture), divided by the sites. Reported as roofline.traffic when the autotuner
@@ -57,7 +58,7 @@ TRAFFIC_B_PER_SITE = {("fp32", 2): 268.5, ("fp32", 11): 467.8, ("fp64", 7): 836.
 SPLIT_VARIANTS = (10, 11)
 BYTES_PER_LUP_SPLIT = {"fp64": 3 * 33 * 8 + 2 * (4 * 8 + 8), "fp32": 3 * 33 * 4 + 2 * (4 * 8 + 4)}
 # Minimum HBM bytes per site update: read and write all 33 f once.
-BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4}
+BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4, "fneq32": 2 * (33 * 4 + 4 * 8)}
 # FP64 instructions (DADD + DFMA + DMUL) per amplification-matrix spectrum of the von Neumann
 # tool on the Sec. 4 sweep: ncu thread-level counts of k_vn divided by the cases. They include the
 # rotation parameters every lane computes alike, so they bound the algorithmic work from above.
@@ -428,7 +429,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="riemann4096",
                     choices=["riemann4096", "reflection1200x300", "shock4000x4", "sod400x4", "vn_sec4"])
-    ap.add_argument("--prec", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default=None, choices=["fp32", "fp64", "fneq32"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
@@ -459,7 +460,7 @@ def main():
             dist.destroy_process_group()
         return
     prec_name = args.prec or ("fp64" if args.workload == "sod400x4" else "fp32")
-    prec = F.FDLBM_FP64 if prec_name == "fp64" else F.FDLBM_FP32_STORE
+    prec = {"fp64": F.FDLBM_FP64, "fp32": F.FDLBM_FP32_STORE, "fneq32": F.FDLBM_FNEQ32}[prec_name]
 
     w = make_workload(args.workload, seed=rank, small=args.small, n=args.n)
     stream = torch.cuda.Stream()
@@ -533,14 +534,16 @@ def main():
         "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec_name == "fp64" else "f32-store/fixed-point+f64-moments/f64-feq",
+        "dtype": {"fp64": "f64", "fp32": "f32-store/fixed-point+f64-moments/f64-feq",
+                  "fneq32": "f64-macros+f32-fneq/f64-step"}[prec_name],
         "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "precision": prec_name,
                    "tile_variant": variant, "autotune_ms": [round(t, 4) for t in times],
-                   "l2": "inputs larger than L2 (f pair %.2f GB)" % (2 * 33 * w.nx * w.ny * (8 if prec_name == "fp64" else 4) / 1e9)
+                   "l2": "inputs larger than L2 (f pair %.2f GB)" % (BYTES_PER_LUP[prec_name] * w.nx * w.ny / 1e9)
                    if w.nx * w.ny * 33 * 4 > 129e6 else "inputs smaller than L2: steps read a warm cache",
                    "status": status, "parallelism": "replicas%d" % world},
-        "roofline": {"bound": "alu", "kernel": "k_moments + k_update (split step)" if split else "k_step (fused step)",
+        "roofline": {"bound": "alu", "kernel": "k_step_fneq (FNEQ32 step)" if prec_name == "fneq32" else
+                     "k_moments + k_update (split step)" if split else "k_step (fused step)",
                      "achieved": achieved,
                      "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak,
                      "traffic": traffic, "traffic_unit": "bytes per step (ncu DRAM read + write of its launches)",

@@ -64,8 +64,12 @@ enum fdlbm_status {
  *  OUTFLOW   zero gradient: both ghost layers copy the nearest interior node;
  *  DIRICHLET ghosts hold f_eq of the state given by fdlbm_set_boundary_state (default rho=1,u=v=0,T=1);
  *  WALL      specular reflection: ghost node -1-j mirrors node j with the normal
- *            velocity component reversed (needs n >= 2 along that axis). */
-enum fdlbm_bc { FDLBM_BC_PERIODIC = 0, FDLBM_BC_OUTFLOW = 1, FDLBM_BC_DIRICHLET = 2, FDLBM_BC_WALL = 3 };
+ *            velocity component reversed (needs n >= 2 along that axis).
+ *  HALO      the side borders another sub-domain of a larger grid: no call of the library writes
+ *            its ghosts; the caller copies the neighbour's two edge rows (or columns) of the
+ *            current state into them between steps (paper_0801_4169_gb300/halo.py). */
+enum fdlbm_bc { FDLBM_BC_PERIODIC = 0, FDLBM_BC_OUTFLOW = 1, FDLBM_BC_DIRICHLET = 2, FDLBM_BC_WALL = 3,
+                FDLBM_BC_HALO = 4 };
 
 enum fdlbm_side { FDLBM_LEFT = 0, FDLBM_RIGHT = 1, FDLBM_BOTTOM = 2, FDLBM_TOP = 3 };
 
@@ -210,6 +214,12 @@ int fdlbm_get_variant(fdlbm_t h);               /* current variant, or a negativ
  * other, which the next real step overwrites. times_ms (may be NULL) receives
  * fdlbm_variant_count() mean launch times in milliseconds. Synchronises the stream. */
 int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms);
+
+/* Which of the handle's two state buffers holds the current state (0: the first, at offset 0 of
+ * its device memory; 1: the second, fbytes further on, fbytes = 33 * pitch * (ny + 4) * element
+ * size rounded up to 256 bytes; FDLBM_FNEQ32 adds its 4 FP64 planes, see enum fdlbm_prec). Waits
+ * for nothing: a caller that reads the buffer orders its reads after the handle's stream. */
+int fdlbm_current_buffer(fdlbm_t h);
 
 /* Steps taken since the last set_macro/load (+ the loaded count). */
 long fdlbm_steps_done(fdlbm_t h);

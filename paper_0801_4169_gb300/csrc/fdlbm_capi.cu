@@ -58,7 +58,7 @@ bool valid_cfg(const fdlbm_config* c, std::string* why) {
   }
   if (c->flags & ~15) { *why = "unknown flag bits"; return false; }
   for (int s = 0; s < 4; ++s)
-    if (c->bc[s] < 0 || c->bc[s] > 3) { *why = "boundary kind out of range"; return false; }
+    if (c->bc[s] < 0 || c->bc[s] > FDLBM_BC_HALO) { *why = "boundary kind out of range"; return false; }
   if ((c->bc[0] == FDLBM_BC_PERIODIC) != (c->bc[1] == FDLBM_BC_PERIODIC)) { *why = "periodic x needs both left and right periodic"; return false; }
   if ((c->bc[2] == FDLBM_BC_PERIODIC) != (c->bc[3] == FDLBM_BC_PERIODIC)) { *why = "periodic y needs both bottom and top periodic"; return false; }
   if ((c->bc[0] == FDLBM_BC_WALL || c->bc[1] == FDLBM_BC_WALL) && c->nx < 2) { *why = "a wall in x needs nx >= 2"; return false; }
@@ -383,7 +383,8 @@ int fdlbm_set_boundary_segment(fdlbm_t h, int side, double c0, double speed, int
   if (h && h->batch) return fail(h, FDLBM_E_STATE, "the solve is a member of a batch (remove it first)");
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (side < 0 || side > 3) return fail(h, FDLBM_E_ARG, "side out of range");
-  if (h->cfg.bc[side] == FDLBM_BC_PERIODIC) return fail(h, FDLBM_E_ARG, "a periodic side takes no segment");
+  if (h->cfg.bc[side] == FDLBM_BC_PERIODIC || h->cfg.bc[side] == FDLBM_BC_HALO)
+    return fail(h, FDLBM_E_ARG, "a periodic or halo side takes no segment");
   if (!std::isfinite(c0) || !std::isfinite(speed)) return fail(h, FDLBM_E_ARG, "c0 and speed must be finite");
   if (!(rho > 0) || !(T > 0) || !std::isfinite(u) || !std::isfinite(v) || !std::isfinite(rho) || !std::isfinite(T))
     return fail(h, FDLBM_E_ARG, "segment state needs finite rho > 0, T > 0");
@@ -721,6 +722,11 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
 }
 
 long fdlbm_steps_done(fdlbm_t h) { return h ? h->steps : -1; }
+
+int fdlbm_current_buffer(fdlbm_t h) {
+  if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
+  return h->cur;
+}
 
 unsigned fdlbm_health(fdlbm_t h) {
   if (!h) return 0;

@@ -26,7 +26,7 @@ __host__ __device__ constexpr double speed(int k) { return speed_c(k) / 100.0; }
 // Scheme flags (same values as enum fdlbm_flags).
 constexpr int F_NO_LW = 1, F_NO_DISP = 2, F_NO_VISC = 4, F_SWITCH_CONST = 8;
 // Boundary kinds (same values as enum fdlbm_bc).
-constexpr int BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_DIRICHLET = 2, BC_WALL = 3;
+constexpr int BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_DIRICHLET = 2, BC_WALL = 3, BC_HALO = 4;
 // Health bits (same values as enum fdlbm_health_bits).
 constexpr unsigned H_NUMERIC = 1u, H_KAPPA = 2u;
 

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfdlbm_gb300.so")
 
 FDLBM_OK, FDLBM_E_ARG, FDLBM_E_OOM, FDLBM_E_CUDA, FDLBM_E_NUMERIC, FDLBM_E_TIMEOUT, FDLBM_E_STATE, FDLBM_E_IO = \
     0, -1, -2, -3, -4, -5, -6, -7
-FDLBM_BC_PERIODIC, FDLBM_BC_OUTFLOW, FDLBM_BC_DIRICHLET, FDLBM_BC_WALL = 0, 1, 2, 3
+FDLBM_BC_PERIODIC, FDLBM_BC_OUTFLOW, FDLBM_BC_DIRICHLET, FDLBM_BC_WALL, FDLBM_BC_HALO = 0, 1, 2, 3, 4
 FDLBM_LEFT, FDLBM_RIGHT, FDLBM_BOTTOM, FDLBM_TOP = 0, 1, 2, 3
 FDLBM_FP64, FDLBM_FP32_STORE, FDLBM_FNEQ32 = 0, 1, 2
 FDLBM_NO_LW, FDLBM_NO_DISP, FDLBM_NO_VISC, FDLBM_SWITCH_CONST = 1, 2, 4, 8
@@ -98,6 +98,7 @@ def lib():
             "fdlbm_get_variant": (ctypes.c_int, [_VP]),
             "fdlbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
             "fdlbm_steps_done": (ctypes.c_long, [_VP]),
+            "fdlbm_current_buffer": (ctypes.c_int, [_VP]),
             "fdlbm_health": (ctypes.c_uint, [_VP]),
             "fdlbm_destroy": (ctypes.c_int, [_VP]),
             "fdlbm_last_error": (ctypes.c_char_p, [_VP]),
@@ -284,6 +285,10 @@ def fdlbm_autotune(h, trial_steps=5):
     times = (ctypes.c_float * n)()
     _check(h, lib().fdlbm_autotune(h, int(trial_steps), times))
     return list(times)
+
+
+def fdlbm_current_buffer(h):
+    return _check(h, lib().fdlbm_current_buffer(h))
 
 
 def fdlbm_steps_done(h):
