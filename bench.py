@@ -46,19 +46,24 @@ sys.path.insert(0, ROOT)
 # work without the moments of the tile ring (see profiles/). FP32 storage sums its moments in
 # 64-bit fixed point on the integer pipes, hence the lower count (FP32 storage: 130 update +
 # 15 moments; FP64: 481 + 89). FNEQ32: ncu's count of k_step_fneq per site (the equilibrium rebuilt
-# on each tile's halo before the stencil and formed again from the new moments).
-FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145, "fneq32": 927}
+# on each tile's halo before the stencil and formed again from the new moments). fp32dw (the
+# double-word equilibrium): 15 moments + 41 FP64 site constants + 14 splits + 1 (ncu: 73.9 with the
+# tile ring's moments).
+FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145, "fneq32": 927, "fp32dw": 71}
 # DRAM bytes (read + write) per site update of one step's launches (k_step, or k_moments +
 # k_update), by (precision, tile variant): ncu dram__bytes_read.sum + dram__bytes_write.sum of one
 # step of this bench's 4096^2 workload (single-pass capture), divided by the sites. Reported as roofline.traffic when the autotuner
 # picks the captured variant, else null.
 TRAFFIC_B_PER_SITE = {("fp32", 2): 268.5, ("fp32", 11): 467.8, ("fp64", 7): 836.7, ("fp64", 10): 873.5}
+DTYPE = {"fp64": "f64", "fp32": "f32-store/fixed-point+f64-moments/f64-feq",
+         "fneq32": "f64-macros+f32-fneq/f64-step", "fp32dw": "f32-store/df32-feq"}
 # Variants that split a step into two launches (moment pass + update pass). Their minimum bytes per
 # site update: f read twice and written once, the moment buffer (4 FP64 + P) written and read.
 SPLIT_VARIANTS = (10, 11)
-BYTES_PER_LUP_SPLIT = {"fp64": 3 * 33 * 8 + 2 * (4 * 8 + 8), "fp32": 3 * 33 * 4 + 2 * (4 * 8 + 4)}
+BYTES_PER_LUP_SPLIT = {"fp64": 3 * 33 * 8 + 2 * (4 * 8 + 8), "fp32": 3 * 33 * 4 + 2 * (4 * 8 + 4),
+                       "fp32dw": 3 * 33 * 4 + 2 * (4 * 8 + 4)}
 # Minimum HBM bytes per site update: read and write all 33 f once.
-BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4, "fneq32": 2 * (33 * 4 + 4 * 8)}
+BYTES_PER_LUP = {"fp64": 2 * 33 * 8, "fp32": 2 * 33 * 4, "fneq32": 2 * (33 * 4 + 4 * 8), "fp32dw": 2 * 33 * 4}
 # FP64 instructions (DADD + DFMA + DMUL) per amplification-matrix spectrum of the von Neumann
 # tool on the Sec. 4 sweep: ncu thread-level counts of k_vn divided by the cases. They include the
 # rotation parameters every lane computes alike, so they bound the algorithmic work from above.
@@ -268,6 +273,38 @@ def posed_states_leg(F, torch, prec, variant, steps=20, warmup=3):
             "status_after": status}
 
 
+def df32_leg(F, torch, w, peaks, sm_mhz, steps=20, warmup=3):
+    """The labelled double-word variant (FDLBM_FP32_STORE_DW, "f32-store/df32-feq") on the same
+    workload: FP32 storage and fixed-point moments as the headline, the per-ring equilibrium
+    constants and pairs in double-word FP32 on the FP32 pipe. Autotuned, timed like the headline."""
+    st = torch.cuda.Stream()
+    s = F.Solver.from_workload(w, F.FDLBM_FP32_STORE_DW, stream=st)
+    times = s.autotune(3)
+    variant = F.fdlbm_get_variant(s.h)
+    s.step(warmup)
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    status = s.sync()
+    s.close()
+    site_rate = w.nx * w.ny / (ms * 1e-3)
+    split = variant in SPLIT_VARIANTS
+    fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * sm_mhz * 1e6 / 1e9
+    fp64 = FP64_OPS_PER_LUP["fp32dw"] * site_rate / 1e9
+    hbm = (BYTES_PER_LUP_SPLIT if split else BYTES_PER_LUP)["fp32dw"] * site_rate / 1e9
+    return {"dtype": DTYPE["fp32dw"], "value": site_rate / 1e9, "unit": "GLUPS", "ms_per_step": ms,
+            "tile_variant": variant, "autotune_ms": [round(t, 4) for t in times], "status": status,
+            "fp64_pipe": {"achieved": fp64, "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": fp64 / fp64_peak},
+            "hbm": {"achieved_gbs": hbm, "peak_gbs": peaks.get("hbm_gbs"), "frac": hbm / peaks.get("hbm_gbs", 6800.0)},
+            "error_vs_fp64_path": "4096^2, 2000 steps, seed 0: L1(rho) 1.82e-7, max |d rho|/max rho 7.2e-6 "
+                                  "(FP64 f_eq: 1.82e-7, 6.8e-6); tests/test_gpu_dw.py checks 512^2"}
+
+
 def serving_leg(n_req=64, steps_scale=0.25, seed=0, budget_bytes=1 << 30):
     """The continuous-batching runtime on a seeded stream of shock-tube solves (the serving
     workload's recipe: Poisson arrivals at 200 requests/s, nx ~ U{256..16384}, ny = 4,
@@ -429,7 +466,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="riemann4096",
                     choices=["riemann4096", "reflection1200x300", "shock4000x4", "sod400x4", "vn_sec4"])
-    ap.add_argument("--prec", default=None, choices=["fp32", "fp64", "fneq32"])
+    ap.add_argument("--prec", default=None, choices=["fp32", "fp64", "fneq32", "fp32dw"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
@@ -460,7 +497,8 @@ def main():
             dist.destroy_process_group()
         return
     prec_name = args.prec or ("fp64" if args.workload == "sod400x4" else "fp32")
-    prec = {"fp64": F.FDLBM_FP64, "fp32": F.FDLBM_FP32_STORE, "fneq32": F.FDLBM_FNEQ32}[prec_name]
+    prec = {"fp64": F.FDLBM_FP64, "fp32": F.FDLBM_FP32_STORE, "fneq32": F.FDLBM_FNEQ32,
+            "fp32dw": F.FDLBM_FP32_STORE_DW}[prec_name]
 
     w = make_workload(args.workload, seed=rank, small=args.small, n=args.n)
     stream = torch.cuda.Stream()
@@ -534,8 +572,7 @@ def main():
         "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32-store/fixed-point+f64-moments/f64-feq",
-                  "fneq32": "f64-macros+f32-fneq/f64-step"}[prec_name],
+        "dtype": DTYPE[prec_name],
         "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "precision": prec_name,
                    "tile_variant": variant, "autotune_ms": [round(t, 4) for t in times],
@@ -561,6 +598,8 @@ def main():
     solver.close()
     if rank == 0 and world == 1 and args.workload == "riemann4096" and not args.small and args.n is None:
         line["posed_states"] = posed_states_leg(F, torch, prec, variant)
+        if prec_name == "fp32":
+            line["variant_df32"] = df32_leg(F, torch, w, peaks, sm_mhz)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.workload, budget_s=20.0)
     if rank == 0 and world == 1 and not args.no_serving and args.workload == "riemann4096" and not args.small:

@@ -89,7 +89,14 @@ enum fdlbm_side { FDLBM_LEFT = 0, FDLBM_RIGHT = 1, FDLBM_BOTTOM = 2, FDLBM_TOP =
  *              fdlbm_get_macro returns the stored macros; fdlbm_get_f returns f_eq + g;
  *              fdlbm_set_f stores the FP64 moments of the given f and its departure from their
  *              equilibrium. Batches of FNEQ32 solves take the 32x4 or 32x8 tile variant. */
-enum fdlbm_prec { FDLBM_FP64 = 0, FDLBM_FP32_STORE = 1, FDLBM_FNEQ32 = 2 };
+enum fdlbm_prec { FDLBM_FP64 = 0, FDLBM_FP32_STORE = 1, FDLBM_FNEQ32 = 2, FDLBM_FP32_STORE_DW = 3 };
+/*  FP32_STORE_DW  a labelled variant of FP32_STORE ("f32-store/df32-feq"): the same storage, exact
+ *              fixed-point moments and FP64 site constants (1/T, projections, F_k(theta), Eqs. 11-13),
+ *              but the per-ring constants and the 16 opposite-direction pairs of Eq. 10 are evaluated
+ *              in double-word FP32 (Dekker products, Knuth sums, compensated Horner) on the FP32 pipe
+ *              instead of the FP64 one. Each f_eq is within about 2^-40 of its FP64 value before it is
+ *              rounded to FP32 storage, so results differ from FP32_STORE by rare last-bit roundings.
+ *              Not FP64 arithmetic; not accepted by fdlbm_batch_add. */
 
 /* Scheme variants of Sec. 4 (Fig. 2, Fig. 3): drop line II, III or IV of Eq. 17,
  * or hold the switch theta_alphaI of Eq. 16 at lambda. Default 0 = full Eq. 17. */

@@ -52,6 +52,7 @@ cudaError_t launch_segment(int prec, void* f, const Grid& g, const Coeffs& c, co
 cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
                         unsigned* health, cudaStream_t s) {
   if (prec == FDLBM_FNEQ32) return launch_step_fneq(variant, f, fn, g, c, health, s);
+  if (prec == FDLBM_FP32_STORE_DW) return launch_step_f32dw(variant, f, fn, g, c, health, s);
   // a tile that holds a y-periodic grid's whole height reuses the interior rows' moments for its
   // ghost rows (same values, bit for bit)
   if (variant >= 0 && variant < V_TILE_COUNT && g.bc[2] == BC_PERIODIC && g.bc[3] == BC_PERIODIC) {

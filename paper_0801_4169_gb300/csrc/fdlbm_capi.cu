@@ -52,8 +52,8 @@ bool valid_cfg(const fdlbm_config* c, std::string* why) {
   if ((long long)c->nx * c->ny > (1LL << 31)) { *why = "nx*ny too large"; return false; }
   if (!(c->dx > 0) || !(c->dy > 0) || !(c->dt > 0) || !(c->tau > 0)) { *why = "dx, dy, dt, tau must be > 0"; return false; }
   if (!(c->lambda >= 0) || !std::isfinite(c->lambda)) { *why = "lambda must be finite and >= 0"; return false; }
-  if (c->prec != FDLBM_FP64 && c->prec != FDLBM_FP32_STORE && c->prec != FDLBM_FNEQ32) {
-    *why = "prec must be FDLBM_FP64, FDLBM_FP32_STORE or FDLBM_FNEQ32";
+  if (c->prec < FDLBM_FP64 || c->prec > FDLBM_FP32_STORE_DW) {
+    *why = "prec must be FDLBM_FP64, FDLBM_FP32_STORE, FDLBM_FNEQ32 or FDLBM_FP32_STORE_DW";
     return false;
   }
   if (c->flags & ~15) { *why = "unknown flag bits"; return false; }
@@ -146,6 +146,15 @@ Coeffs make_coeffs(const fdlbm_config* cfg) {
   c.fkx = (float)c.kx;
   c.fky = (float)c.ky;
   c.flam = (float)c.lam;
+  for (int k = 0; k < 4; ++k) {
+    const double cs[4] = {c.v[k], c.v2h[k], c.v3_6[k], c.v4_24[k]};
+    float(*dst[4])[2] = {c.dv, c.dv2h, c.dv3_6, c.dv4_24};
+    for (int i = 0; i < 4; ++i) {
+      const float hi = (float)cs[i];
+      dst[i][k][0] = hi;
+      dst[i][k][1] = (float)(cs[i] - (double)hi);
+    }
+  }
   return c;
 }
 

@@ -72,6 +72,9 @@ struct Coeffs {
   // FP32 copies used by the FP32-storage stencil
   float fW1[2][4][2], fWm1[2][4][2], fD[2][4][2], fC2[4][3];
   float fr, fkx, fky, flam;
+  // Double-word FP32 (hi + lo) copies of the ring constants v_k, v_k^2/2, v_k^3/6, v_k^4/24 for
+  // FDLBM_FP32_STORE_DW (hi = the FP32 rounding, lo = the rounding of the remainder)
+  float dv[4][2], dv2h[4][2], dv3_6[4][2], dv4_24[4][2];
 };
 
 // One member of a batch (device-resident descriptor table, sorted by tile0).
@@ -119,6 +122,11 @@ cudaError_t launch_step_wrap_f64(int variant, const void* f, void* fn, const Gri
                                  unsigned* health, cudaStream_t s);
 cudaError_t launch_step_wrap_f32(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
                                  unsigned* health, cudaStream_t s);
+// FDLBM_FP32_STORE_DW (fdlbm_step_f32dw.cu): the FP32-storage step with the per-ring equilibrium
+// constants and pairs in double-word FP32. Tile and split variants; the ring-parallel ones map to
+// the 32 x 8 tile.
+cudaError_t launch_step_f32dw(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
+                              cudaStream_t s);
 cudaError_t launch_batch_f64(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,
                              const Coeffs& c, cudaStream_t s);
 cudaError_t launch_batch_f32(int variant, const BatchMember* mem, int nmem, long long tiles, unsigned long long step,

@@ -28,6 +28,7 @@
 //   * the Eq. 17 weights of the +-1 neighbours combined with the node's viscosity once per
 //     (axis, |c| class, ring), shared by the 2-4 directions of that class.
 #include <atomic>
+#include <type_traits>
 
 #include "fdlbm_internal.h"
 
@@ -628,6 +629,118 @@ __device__ __forceinline__ void eq_pair_s<float>(const EqRing& r, double p, doub
 }
 
 // ---------------------------------------------------------------------------------------------
+// Double-word FP32 (FDLBM_FP32_STORE_DW): a value is hi + lo, two FP32 numbers. The site constants
+// stay FP64 (eq_site) and are split into double words; the ring constants are double-word products
+// and the pairs' even and odd parts are evaluated by compensated Horner steps. The building blocks
+// are the error-free transformations of Knuth (TwoSum: a + b = s + e exactly) and of Dekker with a
+// fused multiply-add (a b = p + e exactly, e = fma(a, b, -p)), and the double-word product of
+// Joldes, Muller and Popescu (2017, "DWTimesDW" without the lo*lo term; relative error below 7 u^2,
+// u = 2^-24). The compensated Horner step is that of Graillat, Langlois and Louvet (2005): the
+// running value and the sum of the steps' exact rounding errors, which gives the result as if
+// computed with twice the working precision before the final rounding. Every operation is an
+// explicitly rounded intrinsic, so nothing is contracted or reassociated.
+struct dw {
+  float h, l;
+};
+// x with its 29 low significand bits dropped, as an FP32 number (exact for |x| in the FP32 normal
+// range); 0 below 2^-126, far under any equilibrium value the scheme adds to others.
+__device__ __forceinline__ float f64_trunc32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ah = hi & 0x7fffffffu;
+  const unsigned t = ((ah - (896u << 20)) << 3) | (lo >> 29);
+  return __uint_as_float(ah < (897u << 20) ? 0u : (t | (hi & 0x80000000u)));
+}
+// x = hi + lo: hi its leading 24 bits, lo the (exact, FP64) remainder truncated to FP32, so
+// |x - hi - lo| < 2^-47 |x|. One FP64 operation.
+__device__ __forceinline__ dw split_dw(double x) {
+  dw r;
+  r.h = f64_trunc32(x);
+  const double hi64 = __hiloint2double(__double2hiint(x), (int)((unsigned)__double2loint(x) & 0xe0000000u));
+  r.l = f64_trunc32(__dsub_rn(x, hi64));
+  return r;
+}
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return dw{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ dw mul_dw(dw a, dw b) {
+  const float ch = __fmul_rn(a.h, b.h);
+  const float cl1 = __fmaf_rn(a.h, b.h, -ch);
+  const float cl2 = __fmaf_rn(a.h, b.l, __fmul_rn(a.l, b.h));
+  return fast_two_sum(ch, __fadd_rn(cl1, cl2));
+}
+__device__ __forceinline__ dw dw_of(const float (&c)[2]) { return dw{c[0], c[1]}; }
+// One compensated Horner step, (r + c) <- (r + c) x + a, with x and a double words: r carries the
+// rounded values, c the sum of the exact errors.
+__device__ __forceinline__ void horner_c(float& r, float& c, dw x, dw a) {
+  const float p = __fmul_rn(r, x.h);
+  const float e1 = __fmaf_rn(r, x.h, -p);
+  float s, e2;
+  two_sum(p, a.h, s, e2);
+  c = __fmaf_rn(c, x.h, __fadd_rn(__fadd_rn(e1, e2), __fmaf_rn(r, x.l, a.l)));
+  r = s;
+}
+// (r + c) <- (r + c) x with x a double word
+__device__ __forceinline__ void times_c(float& r, float& c, dw x) {
+  const float p = __fmul_rn(r, x.h);
+  const float e1 = __fmaf_rn(r, x.h, -p);
+  c = __fmaf_rn(c, x.h, __fmaf_rn(r, x.l, e1));
+  r = p;
+}
+struct EqSiteDW {
+  dw A0, A1, p[4], x[4], nF[4];
+  double rest;  // r f_eq of the rest velocity (FP64, as in eq_site)
+};
+__device__ __forceinline__ EqSiteDW eq_site_dw(double n, double ux, double uy, double T, const Coeffs& c) {
+  const EqSite e = eq_site(n, ux, uy, T, c);
+  EqSiteDW d;
+  d.A0 = split_dw(e.A0);
+  d.A1 = split_dw(e.A1);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    d.p[t] = split_dw(e.p[t]);
+    d.x[t] = split_dw(e.x[t]);
+    d.nF[t] = split_dw(e.nF[t]);
+  }
+  d.rest = e.rest;
+  return d;
+}
+// The ring constants of eq_ring as double words (6 products).
+struct EqRingDW {
+  dw al, be, ga, de, ep;
+};
+__device__ __forceinline__ EqRingDW eq_ring_dw(const EqSiteDW& e, int k, const Coeffs& c) {
+  const dw nF = k == 0 ? e.nF[0] : k == 1 ? e.nF[1] : k == 2 ? e.nF[2] : e.nF[3];
+  const dw t = mul_dw(nF, e.A1);
+  EqRingDW r;
+  r.al = mul_dw(nF, e.A0);
+  r.be = mul_dw(t, dw_of(c.dv2h[k]));
+  r.ga = mul_dw(nF, dw_of(c.dv4_24[k]));
+  r.de = mul_dw(t, dw_of(c.dv[k]));
+  r.ep = mul_dw(nF, dw_of(c.dv3_6[k]));
+  return r;
+}
+// r f_eq for the pair with projection p (x = p^2): NE = alpha + x (beta + gamma x) and
+// NO = p (delta + eps x) by compensated Horner steps, each rounded to FP32 once; the pair is then
+// formed in FP32 as in eq_pair_s<float>.
+__device__ __forceinline__ void eq_pair_dw(const EqRingDW& r, dw p, dw x, float& fp, float& fm) {
+  float ne = r.ga.h, nc = r.ga.l;
+  horner_c(ne, nc, x, r.be);
+  horner_c(ne, nc, x, r.al);
+  float no = r.ep.h, oc = r.ep.l;
+  horner_c(no, oc, x, r.de);
+  times_c(no, oc, p);
+  const float e = __fadd_rn(ne, nc), o = __fadd_rn(no, oc);
+  fp = e + o;
+  fm = e - o;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Stencil of Eq. 17 for one velocity (storage precision S):
 //   f_new = W0 f_I + r f_eq + sum_alpha [ W+ f_{I+1} + W- f_{I-1} + D (f_{I+2} - f_{I-2}) ]
 // W0 = 1 - r - sum_alpha (c_alpha^2 [line II] + 2 nu_alpha [line IV]),
@@ -694,11 +807,12 @@ struct StencilConsts<float> {
   __device__ static float lam(const Coeffs& c) { return c.flam; }
 };
 
-// Update of all 33 velocities at one interior node, given its moments and nu_x, nu_y.
-template <typename S>
+// Update of all 33 velocities at one interior node, given its moments and nu_x, nu_y. ES is the
+// equilibrium's site constants: EqSite, or EqSiteDW for the double-word variant (S = float).
+template <typename S, typename ES = EqSite>
 __device__ __forceinline__ void update_ring(int K, const S* __restrict__ f, S* __restrict__ fn, const Grid& g,
                                             const Coeffs& c, long long off, int gx, int gy, const GhostOwn& go,
-                                            const EqSite& e, S w0base, S nux, S nuy) {
+                                            const ES& e, S w0base, S nux, S nuy) {
   using SC = StencilConsts<S>;
   RingW<S> w;
 #pragma unroll
@@ -715,27 +829,51 @@ __device__ __forceinline__ void update_ring(int K, const S* __restrict__ f, S* _
   }
   w.nu[0] = nux;
   w.nu[1] = nuy;
-  const EqRing er = eq_ring(e, K, c);
   const S* fq = f + off;
   // All 8 directions of the ring are computed before any store, so the ring is one basic block
   // the compiler can interleave (the ghost-copy branch comes once per ring, not per velocity).
-  S out[8], fp, fm;
-  // pair (d7: 0 deg, d3: 180 deg), projection p_x
-  eq_pair_s<S>(er, e.p[0], e.x[0], fp, fm);
-  out[7] = stencil_dir<S, 7>(fq + (long long)(1 + 8 * K + 7) * g.plane, g.pitch, w, fp);
-  out[3] = stencil_dir<S, 3>(fq + (long long)(1 + 8 * K + 3) * g.plane, g.pitch, w, fm);
-  // pair (d0: 45 deg, d4: 225 deg), projection s(p_x + p_y)
-  eq_pair_s<S>(er, e.p[1], e.x[1], fp, fm);
-  out[0] = stencil_dir<S, 0>(fq + (long long)(1 + 8 * K + 0) * g.plane, g.pitch, w, fp);
-  out[4] = stencil_dir<S, 4>(fq + (long long)(1 + 8 * K + 4) * g.plane, g.pitch, w, fm);
-  // pair (d1: 90 deg, d5: 270 deg), projection p_y
-  eq_pair_s<S>(er, e.p[2], e.x[2], fp, fm);
-  out[1] = stencil_dir<S, 1>(fq + (long long)(1 + 8 * K + 1) * g.plane, g.pitch, w, fp);
-  out[5] = stencil_dir<S, 5>(fq + (long long)(1 + 8 * K + 5) * g.plane, g.pitch, w, fm);
-  // pair (d2: 135 deg, d6: 315 deg), projection s(p_y - p_x)
-  eq_pair_s<S>(er, e.p[3], e.x[3], fp, fm);
-  out[2] = stencil_dir<S, 2>(fq + (long long)(1 + 8 * K + 2) * g.plane, g.pitch, w, fp);
-  out[6] = stencil_dir<S, 6>(fq + (long long)(1 + 8 * K + 6) * g.plane, g.pitch, w, fm);
+  S out[8];
+  if constexpr (std::is_same<ES, EqSiteDW>::value) {
+    S fe[8];
+    const EqRingDW er = eq_ring_dw(e, K, c);
+    eq_pair_dw(er, e.p[0], e.x[0], fe[7], fe[3]);
+    eq_pair_dw(er, e.p[1], e.x[1], fe[0], fe[4]);
+    eq_pair_dw(er, e.p[2], e.x[2], fe[1], fe[5]);
+    eq_pair_dw(er, e.p[3], e.x[3], fe[2], fe[6]);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const S* p = fq + (long long)(1 + 8 * K + d) * g.plane;
+      switch (d) {
+        case 0: out[0] = stencil_dir<S, 0>(p, g.pitch, w, fe[0]); break;
+        case 1: out[1] = stencil_dir<S, 1>(p, g.pitch, w, fe[1]); break;
+        case 2: out[2] = stencil_dir<S, 2>(p, g.pitch, w, fe[2]); break;
+        case 3: out[3] = stencil_dir<S, 3>(p, g.pitch, w, fe[3]); break;
+        case 4: out[4] = stencil_dir<S, 4>(p, g.pitch, w, fe[4]); break;
+        case 5: out[5] = stencil_dir<S, 5>(p, g.pitch, w, fe[5]); break;
+        case 6: out[6] = stencil_dir<S, 6>(p, g.pitch, w, fe[6]); break;
+        default: out[7] = stencil_dir<S, 7>(p, g.pitch, w, fe[7]); break;
+      }
+    }
+  } else {
+    const EqRing er = eq_ring(e, K, c);
+    S fp, fm;
+    // pair (d7: 0 deg, d3: 180 deg), projection p_x
+    eq_pair_s<S>(er, e.p[0], e.x[0], fp, fm);
+    out[7] = stencil_dir<S, 7>(fq + (long long)(1 + 8 * K + 7) * g.plane, g.pitch, w, fp);
+    out[3] = stencil_dir<S, 3>(fq + (long long)(1 + 8 * K + 3) * g.plane, g.pitch, w, fm);
+    // pair (d0: 45 deg, d4: 225 deg), projection s(p_x + p_y)
+    eq_pair_s<S>(er, e.p[1], e.x[1], fp, fm);
+    out[0] = stencil_dir<S, 0>(fq + (long long)(1 + 8 * K + 0) * g.plane, g.pitch, w, fp);
+    out[4] = stencil_dir<S, 4>(fq + (long long)(1 + 8 * K + 4) * g.plane, g.pitch, w, fm);
+    // pair (d1: 90 deg, d5: 270 deg), projection p_y
+    eq_pair_s<S>(er, e.p[2], e.x[2], fp, fm);
+    out[1] = stencil_dir<S, 1>(fq + (long long)(1 + 8 * K + 1) * g.plane, g.pitch, w, fp);
+    out[5] = stencil_dir<S, 5>(fq + (long long)(1 + 8 * K + 5) * g.plane, g.pitch, w, fm);
+    // pair (d2: 135 deg, d6: 315 deg), projection s(p_y - p_x)
+    eq_pair_s<S>(er, e.p[3], e.x[3], fp, fm);
+    out[2] = stencil_dir<S, 2>(fq + (long long)(1 + 8 * K + 2) * g.plane, g.pitch, w, fp);
+    out[6] = stencil_dir<S, 6>(fq + (long long)(1 + 8 * K + 6) * g.plane, g.pitch, w, fm);
+  }
   store_ring<S>(fn, g, gx, gy, go, K, out);
 }
 
@@ -825,10 +963,33 @@ __global__ void k_moments(const S* __restrict__ f, Grid g, Coeffs c, unsigned* _
   M.P[off] = from_d<S>(m.P);
 }
 
-// The 33 r f_eq of one node into a stage s_fe[q][node] (NN nodes per plane).
-template <typename S, int NN>
+// The 33 r f_eq of one node into a stage s_fe[q][node] (NN nodes per plane). DW: the double-word
+// evaluation of the rings (FDLBM_FP32_STORE_DW, S = float).
+template <typename S, int NN, bool DW = false>
 __device__ __forceinline__ void stage_feq(S* __restrict__ s_fe, int node, double n, double ux, double uy, double T,
                                           const Coeffs& c) {
+  if constexpr (DW) {
+    const EqSiteDW e = eq_site_dw(n, ux, uy, T, c);
+    s_fe[node] = to_s<S>(e.rest);
+#pragma unroll
+    for (int K = 0; K < 4; ++K) {
+      const EqRingDW er = eq_ring_dw(e, K, c);
+      S fp, fm;
+      eq_pair_dw(er, e.p[0], e.x[0], fp, fm);
+      s_fe[(1 + 8 * K + 7) * NN + node] = fp;
+      s_fe[(1 + 8 * K + 3) * NN + node] = fm;
+      eq_pair_dw(er, e.p[1], e.x[1], fp, fm);
+      s_fe[(1 + 8 * K + 0) * NN + node] = fp;
+      s_fe[(1 + 8 * K + 4) * NN + node] = fm;
+      eq_pair_dw(er, e.p[2], e.x[2], fp, fm);
+      s_fe[(1 + 8 * K + 1) * NN + node] = fp;
+      s_fe[(1 + 8 * K + 5) * NN + node] = fm;
+      eq_pair_dw(er, e.p[3], e.x[3], fp, fm);
+      s_fe[(1 + 8 * K + 2) * NN + node] = fp;
+      s_fe[(1 + 8 * K + 6) * NN + node] = fm;
+    }
+    return;
+  }
   const EqSite e = eq_site(n, ux, uy, T, c);
   s_fe[node] = to_s<S>(e.rest);
 #pragma unroll
@@ -853,9 +1014,12 @@ __device__ __forceinline__ void stage_feq(S* __restrict__ s_fe, int node, double
 // WRAPY (batched kernel): a tile that holds a y-periodic grid's whole height takes its two ghost
 // rows' moments from the interior rows they copy (bit for bit the same values) instead of summing
 // them again: 4-row serving tubes in 32 x 4 tiles sum 4 rows of moments instead of 6.
-template <typename S, int BX, int BY, int RY, bool FROM_BUF = false, bool WRAPY = false, bool STAGE = false>
+// DW (S = float only): the double-word equilibrium of FDLBM_FP32_STORE_DW.
+template <typename S, int BX, int BY, int RY, bool FROM_BUF = false, bool WRAPY = false, bool STAGE = false,
+          bool DW = false>
 __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict__ fn, const Grid& g, const Coeffs& c,
                                           unsigned* __restrict__ health, int tx, int ty, S* s_fe = nullptr) {
+  static_assert(!DW || std::is_same<S, float>::value, "the double-word equilibrium is for FP32 storage");
   constexpr int TW = BX, TH = BY * RY, SW = TW + 2, SH = TH + 2, NT = BX * BY;
   using SC = StencilConsts<S>;
   // P is staged in the storage precision: the switch of Eq. 16 is a limiter coefficient, and in
@@ -934,7 +1098,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + rr * BY;
       if (gx >= g.nx || gy >= g.ny) continue;
       const int node = (threadIdx.y + rr * BY) * TW + threadIdx.x;
-      stage_feq<S, NN>(s_fe, node, s_n[ly][lx], s_ux[ly][lx], s_uy[ly][lx], s_T[ly][lx], c);
+      stage_feq<S, NN, DW>(s_fe, node, s_n[ly][lx], s_ux[ly][lx], s_uy[ly][lx], s_T[ly][lx], c);
     }
     __syncthreads();
 #pragma unroll 1
@@ -1006,7 +1170,10 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       snuy = (S)0.5 * thy * aky * ((S)1 - aky);
     }
     const S w0base = ((S)1 - SC::r(c)) - (S)2 * (snux + snuy);
-    const EqSite e = eq_site(n, ux, uy, T, c);
+    using ES = typename std::conditional<DW, EqSiteDW, EqSite>::type;
+    ES e;
+    if constexpr (DW) e = eq_site_dw(n, ux, uy, T, c);
+    else e = eq_site(n, ux, uy, T, c);
     const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
     const GhostOwn go = ghost_own(g, gx, gy);
     // rest velocity: f_eq = n F_0 A0; c = 0 on both axes (line IV only)
@@ -1018,10 +1185,10 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       acc = fma(snuy, ld(p + g.pitch) + ld(p - g.pitch), acc);
       store_node<S, 0>(fn, g, gx, gy, go, acc);
     }
-    update_ring<S>(0, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
-    update_ring<S>(1, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
-    update_ring<S>(2, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
-    update_ring<S>(3, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S, ES>(0, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S, ES>(1, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S, ES>(2, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S, ES>(3, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
   }
   }
   if (bits) atomicOr(health, bits);
@@ -1036,20 +1203,20 @@ template <typename S, int TW, int TH, bool STAGE>
 constexpr int stage_bytes() {
   return STAGE && sizeof(S) == 4 ? Q * TW * TH * (int)sizeof(S) : 0;
 }
-template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false, bool STAGE = false>
+template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false, bool STAGE = false, bool DW = false>
 __global__ void __launch_bounds__(BX * BY, MINB) k_step(const S* __restrict__ f, S* __restrict__ fn, Grid g, Coeffs c,
                                                   unsigned* __restrict__ health) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
-  step_tile<S, BX, BY, RY, false, WRAPY, STAGE && sizeof(S) == 4>(f, fn, g, c, health, blockIdx.x, blockIdx.y,
-                                                                  reinterpret_cast<S*>(s_dyn));
+  step_tile<S, BX, BY, RY, false, WRAPY, STAGE && sizeof(S) == 4, DW>(f, fn, g, c, health, blockIdx.x, blockIdx.y,
+                                                                      reinterpret_cast<S*>(s_dyn));
 }
 // Split step, pass 2: the update with the tile's moments read from the moment buffer.
-template <typename S, int BX, int BY, int RY, int MINB, bool STAGE = false>
+template <typename S, int BX, int BY, int RY, int MINB, bool STAGE = false, bool DW = false>
 __global__ void __launch_bounds__(BX * BY, MINB) k_update(const S* __restrict__ f, S* __restrict__ fn, Grid g,
                                                     Coeffs c, unsigned* __restrict__ health) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
-  step_tile<S, BX, BY, RY, true, false, STAGE && sizeof(S) == 4>(f, fn, g, c, health, blockIdx.x, blockIdx.y,
-                                                                 reinterpret_cast<S*>(s_dyn));
+  step_tile<S, BX, BY, RY, true, false, STAGE && sizeof(S) == 4, DW>(f, fn, g, c, health, blockIdx.x, blockIdx.y,
+                                                                     reinterpret_cast<S*>(s_dyn));
 }
 
 // Batched step: every member solve of a batch advances one time step in one launch. Members share
@@ -1302,17 +1469,17 @@ cudaError_t allow_dynamic_smem(K kernel, int bytes, std::atomic<unsigned long lo
   return e;
 }
 
-template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false, bool STAGE = false>
+template <typename S, int BX, int BY, int RY, int MINB, bool WRAPY = false, bool STAGE = false, bool DW = false>
 cudaError_t launch_step_t(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
   constexpr int smem = stage_bytes<S, BX, BY * RY, STAGE>();
   static std::atomic<unsigned long long> attr{0};  // devices already opted in
-  const cudaError_t e = allow_dynamic_smem(k_step<S, BX, BY, RY, MINB, WRAPY, STAGE>, smem, attr);
+  const cudaError_t e = allow_dynamic_smem(k_step<S, BX, BY, RY, MINB, WRAPY, STAGE, DW>, smem, attr);
   if (e != cudaSuccess) return e;
   dim3 block(BX, BY);
   dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY * RY - 1) / (BY * RY));
-  k_step<S, BX, BY, RY, MINB, WRAPY, STAGE><<<grid, block, smem, s>>>(static_cast<const S*>(f), static_cast<S*>(fn),
-                                                                      g, c, health);
+  k_step<S, BX, BY, RY, MINB, WRAPY, STAGE, DW><<<grid, block, smem, s>>>(static_cast<const S*>(f),
+                                                                          static_cast<S*>(fn), g, c, health);
   return cudaGetLastError();
 }
 
@@ -1346,38 +1513,44 @@ cudaError_t launch_rp_t(const void* f, void* fn, const Grid& g, const Coeffs& c,
   return cudaGetLastError();
 }
 
-template <typename S, int BX, int BY, int RY, int MINB, bool STAGE = false>
+template <typename S, int BX, int BY, int RY, int MINB, bool STAGE = false, bool DW = false>
 cudaError_t launch_split_t(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health, cudaStream_t s) {
   if (!g.mom) return cudaErrorInvalidValue;
   constexpr int smem = stage_bytes<S, BX, BY * RY, STAGE>();
   static std::atomic<unsigned long long> attr{0};  // devices already opted in
-  const cudaError_t e = allow_dynamic_smem(k_update<S, BX, BY, RY, MINB, STAGE>, smem, attr);
+  const cudaError_t e = allow_dynamic_smem(k_update<S, BX, BY, RY, MINB, STAGE, DW>, smem, attr);
   if (e != cudaSuccess) return e;
   dim3 mb(32, 8), mg((g.nx + 2 + 31) / 32, (g.ny + 2 + 7) / 8);
   k_moments<S><<<mg, mb, 0, s>>>(static_cast<const S*>(f), g, c, health);
   dim3 block(BX, BY);
   dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY * RY - 1) / (BY * RY));
-  k_update<S, BX, BY, RY, MINB, STAGE><<<grid, block, smem, s>>>(static_cast<const S*>(f), static_cast<S*>(fn), g,
-                                                                 c, health);
+  k_update<S, BX, BY, RY, MINB, STAGE, DW><<<grid, block, smem, s>>>(static_cast<const S*>(f), static_cast<S*>(fn),
+                                                                     g, c, health);
   return cudaGetLastError();
 }
 
-template <typename S>
+// DW: the double-word equilibrium (FDLBM_FP32_STORE_DW, S = float); it has no ring-parallel kernel,
+// so those variants take the 32 x 8 tile.
+template <typename S, bool DW = false>
 cudaError_t launch_step_v(int variant, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                           cudaStream_t s) {
   switch (variant) {
-    case V_S32x16: return launch_split_t<S, 32, 8, 2, 2, true>(f, fn, g, c, health, s);
-    case V_S32x32: return launch_split_t<S, 32, 8, 4, 2>(f, fn, g, c, health, s);
-    case V_RP16x4: return launch_rp_t<S, 16, 4>(f, fn, g, c, health, s);
-    case V_RP8x4: return launch_rp_t<S, 8, 4>(f, fn, g, c, health, s);
-    case V_T32x4: return launch_step_t<S, 32, 4, 1, 4>(f, fn, g, c, health, s);
-    case V_T32x8: return launch_step_t<S, 32, 4, 2, 4>(f, fn, g, c, health, s);
-    case V_T32x16: return launch_step_t<S, 32, 8, 2, 2, false, true>(f, fn, g, c, health, s);
-    case V_T16x4: return launch_step_t<S, 16, 4, 1, 1>(f, fn, g, c, health, s);
-    case V_T64x8: return launch_step_t<S, 64, 4, 2, 2, false, true>(f, fn, g, c, health, s);
-    case V_T32x32: return launch_step_t<S, 32, 8, 4, 2>(f, fn, g, c, health, s);
-    case V_T32x24: return launch_step_t<S, 32, 4, 6, 4>(f, fn, g, c, health, s);
-    case V_T32x28: return launch_step_t<S, 32, 4, 7, 4>(f, fn, g, c, health, s);
+    case V_S32x16: return launch_split_t<S, 32, 8, 2, 2, true, DW>(f, fn, g, c, health, s);
+    case V_S32x32: return launch_split_t<S, 32, 8, 4, 2, false, DW>(f, fn, g, c, health, s);
+    case V_RP16x4:
+      if constexpr (DW) return launch_step_t<S, 32, 4, 2, 4, false, false, DW>(f, fn, g, c, health, s);
+      else return launch_rp_t<S, 16, 4>(f, fn, g, c, health, s);
+    case V_RP8x4:
+      if constexpr (DW) return launch_step_t<S, 32, 4, 2, 4, false, false, DW>(f, fn, g, c, health, s);
+      else return launch_rp_t<S, 8, 4>(f, fn, g, c, health, s);
+    case V_T32x4: return launch_step_t<S, 32, 4, 1, 4, false, false, DW>(f, fn, g, c, health, s);
+    case V_T32x8: return launch_step_t<S, 32, 4, 2, 4, false, false, DW>(f, fn, g, c, health, s);
+    case V_T32x16: return launch_step_t<S, 32, 8, 2, 2, false, true, DW>(f, fn, g, c, health, s);
+    case V_T16x4: return launch_step_t<S, 16, 4, 1, 1, false, false, DW>(f, fn, g, c, health, s);
+    case V_T64x8: return launch_step_t<S, 64, 4, 2, 2, false, true, DW>(f, fn, g, c, health, s);
+    case V_T32x32: return launch_step_t<S, 32, 8, 4, 2, false, false, DW>(f, fn, g, c, health, s);
+    case V_T32x24: return launch_step_t<S, 32, 4, 6, 4, false, false, DW>(f, fn, g, c, health, s);
+    case V_T32x28: return launch_step_t<S, 32, 4, 7, 4, false, false, DW>(f, fn, g, c, health, s);
     default: return cudaErrorInvalidValue;
   }
 }
