@@ -70,7 +70,23 @@ struct GpuEngine : Engine {
   cudaStream_t stream = nullptr;
   bool separate = false;  // baseline: every solve stepped with its own launches, no batches
   std::map<std::tuple<double, double, double, double, double, int, int>, fdlbm_batch_t> batches;
+  std::map<fdlbm_batch_t, int> tuned_size;  // members when the batch's tile was last autotuned
   GpuEngine(cudaStream_t s, bool sep) : stream(s), separate(sep) {}
+  // The batch's tile variant from the autotuner (trial launches on the members' current states,
+  // which do not advance them), when the batch is first stepped and again whenever its membership
+  // has doubled or halved since.
+  int tune(fdlbm_batch_t b, std::string* err) {
+    const int n = fdlbm_batch_size(b);
+    auto it = tuned_size.find(b);
+    if (n < 1 || (it != tuned_size.end() && n < 2 * it->second && 2 * n > it->second)) return FDLBM_OK;
+    const int rc = fdlbm_batch_autotune(b, 2, nullptr);
+    if (rc) {
+      *err = fdlbm_batch_last_error(b);
+      return rc;
+    }
+    tuned_size[b] = n;
+    return FDLBM_OK;
+  }
   ~GpuEngine() override {
     for (auto& kv : batches) fdlbm_batch_destroy(kv.second);
   }
@@ -125,7 +141,9 @@ struct GpuEngine : Engine {
     }
     for (auto& kv : batches) {
       if (fdlbm_batch_size(kv.second) <= 0) continue;
-      int rc = fdlbm_batch_step(kv.second, k);
+      int rc = tune(kv.second, err);
+      if (rc) return rc;
+      rc = fdlbm_batch_step(kv.second, k);
       if (rc) {
         *err = fdlbm_batch_last_error(kv.second);
         return rc;

@@ -488,6 +488,27 @@ def test_fp32_storage_l1_against_the_fp64_path(seed):
     assert np.mean(np.abs(r32 - r64)) / np.mean(np.abs(r64)) <= 1e-5
 
 
+def test_fp32_storage_error_at_full_size():
+    """The headline workload itself: the 4096^2 four-quadrant problem, seed 0, 2000 steps, FP32
+    storage (FP64 f_eq and its double-word variant) against the FP64 GPU path. L1(rho) measures
+    1.82e-7 for both and max |d rho| / max rho 6.8e-6 (FP64 f_eq) and 7.2e-6 (double word); bounds
+    1e-6 and 1e-5."""
+    w = W.riemann4q(n=4096, seed=0)
+    rho = {}
+    for prec in (F.FDLBM_FP64, F.FDLBM_FP32_STORE, F.FDLBM_FP32_STORE_DW):
+        s = F.Solver.from_workload(w, prec)
+        s.set_variant(10 if prec == F.FDLBM_FP64 else 2)  # the autotuner's choices at this size
+        s.step(w.steps)
+        rho[prec] = s.get_macro()[0]
+        assert s.sync() == 0
+        s.close()
+    r64 = rho[F.FDLBM_FP64]
+    for prec in (F.FDLBM_FP32_STORE, F.FDLBM_FP32_STORE_DW):
+        d = np.abs(rho[prec] - r64)
+        assert np.mean(d) / np.mean(r64) <= 1e-6
+        assert np.max(d) / np.max(r64) <= 1e-5
+
+
 def test_reflection_downscale_matches_oracle_within_its_rounding_spread():
     """The C3 reflection on its 300 x 75 downscale, FP64, 400 steps: GPU and oracle moments agree to
     3x the oracle's own spread under 4-ulp per-step perturbations of f (kappa = 7.4e6 in the top
