@@ -54,7 +54,8 @@ FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145, "fneq32": 927, "fp32dw": 71}
 # k_update), by (precision, tile variant): ncu dram__bytes_read.sum + dram__bytes_write.sum of one
 # step of this bench's 4096^2 workload (single-pass capture), divided by the sites. Reported as roofline.traffic when the autotuner
 # picks the captured variant, else null.
-TRAFFIC_B_PER_SITE = {("fp32", 2): 268.5, ("fp32", 11): 467.8, ("fp64", 7): 836.7, ("fp64", 10): 873.5}
+TRAFFIC_B_PER_SITE = {("fp32", 2): 268.5, ("fp32", 6): 267.5, ("fp32", 11): 467.8, ("fp64", 7): 836.7,
+                      ("fp64", 10): 873.5, ("fp32dw", 6): 265.7}
 DTYPE = {"fp64": "f64", "fp32": "f32-store/fixed-point+f64-moments/f64-feq",
          "fneq32": "f64-macros+f32-fneq/f64-step", "fp32dw": "f32-store/df32-feq"}
 # Variants that split a step into two launches (moment pass + update pass). Their minimum bytes per
@@ -301,6 +302,8 @@ def df32_leg(F, torch, w, peaks, sm_mhz, steps=20, warmup=3):
             "tile_variant": variant, "autotune_ms": [round(t, 4) for t in times], "status": status,
             "fp64_pipe": {"achieved": fp64, "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": fp64 / fp64_peak},
             "hbm": {"achieved_gbs": hbm, "peak_gbs": peaks.get("hbm_gbs"), "frac": hbm / peaks.get("hbm_gbs", 6800.0)},
+            "traffic": (TRAFFIC_B_PER_SITE.get(("fp32dw", variant), 0) * w.nx * w.ny or None)
+            if (w.nx, w.ny) == (4096, 4096) else None,
             "error_vs_fp64_path": "4096^2, 2000 steps, seed 0: L1(rho) 1.82e-7, max |d rho|/max rho 7.2e-6 "
                                   "(FP64 f_eq: 1.82e-7, 6.8e-6); tests/test_gpu_dw.py checks 512^2"}
 
