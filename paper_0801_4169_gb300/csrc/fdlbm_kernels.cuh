@@ -1549,7 +1549,7 @@ cudaError_t launch_step_v(int variant, const void* f, void* fn, const Grid& g, c
     case V_T16x4: return launch_step_t<S, 16, 4, 1, 1, false, false, DW>(f, fn, g, c, health, s);
     case V_T64x8: return launch_step_t<S, 64, 4, 2, 2, false, true, DW>(f, fn, g, c, health, s);
     case V_T32x32:
-      if constexpr (DW) return launch_step_t<S, 32, 4, 1, 6, false, true, DW>(f, fn, g, c, health, s);
+      if constexpr (std::is_same<S, float>::value) return launch_step_t<S, 32, 4, 1, 6, false, true, DW>(f, fn, g, c, health, s);
       else return launch_step_t<S, 32, 8, 4, 2>(f, fn, g, c, health, s);
     case V_T32x24:
       // FP32 storage: a staged 32 x 8 tile at <= 85 registers for 3 CTAs per SM (24 warps); FP64
@@ -1557,7 +1557,7 @@ cudaError_t launch_step_v(int variant, const void* f, void* fn, const Grid& g, c
       if constexpr (std::is_same<S, float>::value) return launch_step_t<S, 32, 8, 1, 3, false, true, DW>(f, fn, g, c, health, s);
       else return launch_step_t<S, 32, 4, 6, 4>(f, fn, g, c, health, s);
     case V_T32x28:
-      if constexpr (DW) return launch_step_t<S, 32, 8, 1, 4, false, true, DW>(f, fn, g, c, health, s);
+      if constexpr (std::is_same<S, float>::value) return launch_step_t<S, 32, 8, 1, 4, false, true, DW>(f, fn, g, c, health, s);
       else return launch_step_t<S, 32, 4, 7, 4>(f, fn, g, c, health, s);
     default: return cudaErrorInvalidValue;
   }
