@@ -244,12 +244,13 @@ int init_from_device_macros(fdlbm_ctx* h, const double* rho, const double* u, co
   poll_health(h, true);
   cudaError_t e = cudaMemsetAsync(h->d_health, 0, sizeof(unsigned), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "health reset");
-  // both buffers get f_eq so ghost regions never hold stale data
-  for (int b = 0; b < 2; ++b) {
-    e = h->cfg.prec == FDLBM_FNEQ32 ? launch_init_fneq(h->f[b], h->grid, h->coeffs, rho, u, v, T, h->stream)
-                                    : launch_init(h->cfg.prec, h->f[b], h->grid, h->coeffs, rho, u, v, T, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "init launch");
-  }
+  // The current buffer gets f_eq with its ghost ring. The other one needs only its Dirichlet ghosts
+  // and segments (fill_ghosts_dirichlet writes both buffers'): the first step writes its interior
+  // and every ghost an interior node owns, halo ghosts come from the caller, and ghost corners are
+  // never read.
+  e = h->cfg.prec == FDLBM_FNEQ32 ? launch_init_fneq(h->f[0], h->grid, h->coeffs, rho, u, v, T, h->stream)
+                                  : launch_init(h->cfg.prec, h->f[0], h->grid, h->coeffs, rho, u, v, T, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "init launch");
   int rc = fill_ghosts_dirichlet(h, 0);
   if (rc) return rc;
   h->cur = 0;

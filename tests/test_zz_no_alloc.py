@@ -43,7 +43,8 @@ def _interior(buf, cfg):
 
 
 def _copies(solver):
-    """Two caller-owned device buffers holding the handle's current pair (both initialised)."""
+    """Two caller-owned device buffers holding the handle's pair: the current state and the
+    second buffer, whose interior the first step writes (both carry the Dirichlet ghosts)."""
     _, _, _, fbytes = _layout(solver.cfg)
     off = solver.mem_offset
     bufs = []
