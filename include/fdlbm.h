@@ -90,11 +90,11 @@ enum fdlbm_side { FDLBM_LEFT = 0, FDLBM_RIGHT = 1, FDLBM_BOTTOM = 2, FDLBM_TOP =
  *              fdlbm_set_f stores the FP64 moments of the given f and its departure from their
  *              equilibrium. Batches of FNEQ32 solves take the 32x4 or 32x8 tile variant. */
 enum fdlbm_prec { FDLBM_FP64 = 0, FDLBM_FP32_STORE = 1, FDLBM_FNEQ32 = 2, FDLBM_FP32_STORE_DW = 3 };
-/*  FP32_STORE_DW  a labelled variant of FP32_STORE ("f32-store/df32-feq"): the same storage, exact
- *              fixed-point moments and FP64 site constants (1/T, projections, F_k(theta), Eqs. 11-13),
- *              but the per-ring constants and the 16 opposite-direction pairs of Eq. 10 are evaluated
- *              in double-word FP32 (Dekker products, Knuth sums, compensated Horner) on the FP32 pipe
- *              instead of the FP64 one. Each f_eq is within about 2^-40 of its FP64 value before it is
+/*  FP32_STORE_DW  a labelled variant of FP32_STORE ("f32-store/df32-feq"): the same storage and exact
+ *              fixed-point moments finished in FP64, but the equilibrium (Eqs. 10-13: 1/T, the
+ *              projections, A0, A1, F_k(theta), the per-ring constants and the 16 opposite-direction
+ *              pairs) is evaluated in double-word FP32 (Dekker products, Knuth sums, compensated
+ *              Horner) on the FP32 pipe instead of the FP64 one. Each f_eq is within about 2^-40 of its FP64 value before it is
  *              rounded to FP32 storage, so results differ from FP32_STORE by rare last-bit roundings.
  *              Not FP64 arithmetic; not accepted by fdlbm_batch_add. */
 

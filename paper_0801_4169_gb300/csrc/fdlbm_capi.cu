@@ -146,15 +146,20 @@ Coeffs make_coeffs(const fdlbm_config* cfg) {
   c.fkx = (float)c.kx;
   c.fky = (float)c.ky;
   c.flam = (float)c.lam;
+  auto split = [](double x, float* out) {
+    const float hi = (float)x;
+    out[0] = hi;
+    out[1] = (float)(x - (double)hi);
+  };
   for (int k = 0; k < 4; ++k) {
-    const double cs[4] = {c.v[k], c.v2h[k], c.v3_6[k], c.v4_24[k]};
-    float(*dst[4])[2] = {c.dv, c.dv2h, c.dv3_6, c.dv4_24};
-    for (int i = 0; i < 4; ++i) {
-      const float hi = (float)cs[i];
-      dst[i][k][0] = hi;
-      dst[i][k][1] = (float)(cs[i] - (double)hi);
-    }
+    split(c.v[k], c.dv[k]);
+    split(c.v2h[k], c.dv2h[k]);
+    split(c.v3_6[k], c.dv3_6[k]);
+    split(c.v4_24[k], c.dv4_24[k]);
+    for (int i = 0; i < 4; ++i) split(c.Fh[k][i], c.dFh[k][i]);
   }
+  split(c.r, c.dr);
+  split(s, c.dkS);
   return c;
 }
 

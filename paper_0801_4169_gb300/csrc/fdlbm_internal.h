@@ -75,6 +75,8 @@ struct Coeffs {
   // Double-word FP32 (hi + lo) copies of the ring constants v_k, v_k^2/2, v_k^3/6, v_k^4/24 for
   // FDLBM_FP32_STORE_DW (hi = the FP32 rounding, lo = the rounding of the remainder)
   float dv[4][2], dv2h[4][2], dv3_6[4][2], dv4_24[4][2];
+  // ... and of the F_k polynomials' coefficients, dt/tau and sqrt(1/2)
+  float dFh[4][4][2], dr[2], dkS[2];
 };
 
 // One member of a batch (device-resident descriptor table, sorted by tile0).

@@ -692,23 +692,67 @@ __device__ __forceinline__ void times_c(float& r, float& c, dw x) {
   c = __fmaf_rn(c, x.h, __fmaf_rn(r, x.l, e1));
   r = p;
 }
+// Double-word sum with both operands double words (Joldes, Muller and Popescu 2017,
+// "AccurateDWPlusDW": two TwoSums and two Fast2Sums; relative error below 3 u^2 + 13 u^3, also
+// under cancellation).
+__device__ __forceinline__ dw add_dw(dw a, dw b) {
+  float sh, sl, th, tl;
+  two_sum(a.h, b.h, sh, sl);
+  two_sum(a.l, b.l, th, tl);
+  const dw v = fast_two_sum(sh, __fadd_rn(sl, th));
+  return fast_two_sum(v.h, __fadd_rn(tl, v.l));
+}
+__device__ __forceinline__ dw scale_dw(dw a, float s) {  // s a power of two: exact
+  return dw{__fmul_rn(a.h, s), __fmul_rn(a.l, s)};
+}
+__device__ __forceinline__ dw neg_dw(dw a) { return dw{-a.h, -a.l}; }
+// 1/t for a double word t with t.h normal and positive: the FP32 reciprocal y refined by one Newton
+// step in double-word form, y + y e with e = 1 - t y formed with the exact product error (1 - t.h y is
+// exact by Sterbenz's lemma, t.h y being within an ulp of 1): relative error O(e^2) ~ 2^-46.
+__device__ __forceinline__ dw rcp_dw(dw t) {
+  const float y = __frcp_rn(t.h);
+  const float p = __fmul_rn(t.h, y);
+  const float ep = __fmaf_rn(t.h, y, -p);
+  const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), ep), __fmul_rn(t.l, y));
+  return fast_two_sum(y, __fmul_rn(y, e));
+}
 struct EqSiteDW {
   dw A0, A1, p[4], x[4], nF[4];
-  double rest;  // r f_eq of the rest velocity (FP64, as in eq_site)
+  float rest;  // r f_eq of the rest velocity, rounded to FP32
 };
+// eq_site in double-word FP32 from the FP64 macros (split once each): 1/theta by rcp_dw, the
+// projections and |u|^2/theta by double-word products and sums, A0 and A1 with accurate sums (they
+// cancel when |u|^2/(2 theta) is near 1), and r n F_k = (r n theta) P_k(theta) with each cubic by
+// compensated Horner steps over its double-word coefficients.
 __device__ __forceinline__ EqSiteDW eq_site_dw(double n, double ux, double uy, double T, const Coeffs& c) {
-  const EqSite e = eq_site(n, ux, uy, T, c);
-  EqSiteDW d;
-  d.A0 = split_dw(e.A0);
-  d.A1 = split_dw(e.A1);
+  const dw dn = split_dw(n), dux = split_dw(ux), duy = split_dw(uy), th = split_dw(T);
+  const dw ith = rcp_dw(th);
+  const dw px = mul_dw(dux, ith), py = mul_dw(duy, ith);
+  const dw kS = dw_of(c.dkS);
+  EqSiteDW e;
+  e.p[0] = px;
+  e.p[1] = mul_dw(kS, add_dw(px, py));
+  e.p[2] = py;
+  e.p[3] = mul_dw(kS, add_dw(py, neg_dw(px)));
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    d.p[t] = split_dw(e.p[t]);
-    d.x[t] = split_dw(e.x[t]);
-    d.nF[t] = split_dw(e.nF[t]);
+  for (int t = 0; t < 4; ++t) e.x[t] = mul_dw(e.p[t], e.p[t]);
+  const dw b2 = add_dw(mul_dw(dux, px), mul_dw(duy, py));  // |u|^2 / theta
+  e.A1 = add_dw(dw{1.0f, 0.0f}, scale_dw(neg_dw(b2), 0.5f));
+  e.A0 = add_dw(e.A1, scale_dw(mul_dw(b2, b2), 0.125f));
+  const dw rn = mul_dw(dw_of(c.dr), dn), rnth = mul_dw(rn, th);
+  dw snF = dw{0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float r = c.dFh[k][3][0], cc = c.dFh[k][3][1];
+    horner_c(r, cc, th, dw_of(c.dFh[k][2]));
+    horner_c(r, cc, th, dw_of(c.dFh[k][1]));
+    horner_c(r, cc, th, dw_of(c.dFh[k][0]));
+    e.nF[k] = mul_dw(rnth, fast_two_sum(r, cc));
+    snF = add_dw(snF, e.nF[k]);
   }
-  d.rest = e.rest;
-  return d;
+  const dw rest = mul_dw(add_dw(rn, scale_dw(neg_dw(snF), 8.0f)), e.A0);
+  e.rest = __fadd_rn(rest.h, rest.l);
+  return e;
 }
 // The ring constants of eq_ring as double words (6 products).
 struct EqRingDW {
@@ -970,7 +1014,7 @@ __device__ __forceinline__ void stage_feq(S* __restrict__ s_fe, int node, double
                                           const Coeffs& c) {
   if constexpr (DW) {
     const EqSiteDW e = eq_site_dw(n, ux, uy, T, c);
-    s_fe[node] = to_s<S>(e.rest);
+    s_fe[node] = e.rest;
 #pragma unroll
     for (int K = 0; K < 4; ++K) {
       const EqRingDW er = eq_ring_dw(e, K, c);
@@ -1178,7 +1222,9 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
     const GhostOwn go = ghost_own(g, gx, gy);
     // rest velocity: f_eq = n F_0 A0; c = 0 on both axes (line IV only)
     {
-      const S rfeq = to_s<S>(e.rest);
+      S rfeq;
+      if constexpr (DW) rfeq = e.rest;
+      else rfeq = to_s<S>(e.rest);
       const S* p = f + off;
       S acc = fma(w0base, ld(p), rfeq);
       acc = fma(snux, ld(p + 1) + ld(p - 1), acc);
