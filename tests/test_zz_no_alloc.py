@@ -32,14 +32,31 @@ def _layout(cfg):
     rows = cfg.ny + 4
     esize = 8 if cfg.prec == F.FDLBM_FP64 else 4
     fbytes = (33 * pitch * rows * esize + 255) // 256 * 256
+    if cfg.prec == F.FDLBM_FNEQ32:  # then 4 FP64 planes of the macros
+        fbytes = (fbytes + 4 * pitch * rows * 8 + 255) // 256 * 256
     return pitch, rows, esize, fbytes
 
 
 def _interior(buf, cfg):
+    """The stored values of the interior: f, or for FNEQ32 its departure g (the tests compare the
+    buffers, which the handle and the entry point fill the same way)."""
     pitch, rows, esize, _ = _layout(cfg)
     dt = torch.float64 if esize == 8 else torch.float32
     a = buf[:33 * pitch * rows * esize].view(dt).reshape(33, rows, pitch)
-    return a[:, 2:2 + cfg.ny, 2:2 + cfg.nx].double().cpu().numpy()
+    out = a[:, 2:2 + cfg.ny, 2:2 + cfg.nx].double().cpu().numpy()
+    if cfg.prec == F.FDLBM_FNEQ32:
+        g0 = (33 * pitch * rows * 4 + 255) // 256 * 256
+        m = buf[g0:g0 + 4 * pitch * rows * 8].view(torch.float64).reshape(4, rows, pitch)
+        out = np.concatenate([out, m[:, 2:2 + cfg.ny, 2:2 + cfg.nx].cpu().numpy()])
+    return out
+
+
+def _handle_state(s):
+    """The handle's current buffer, read the same way as the entry point's."""
+    _, _, _, fbytes = _layout(s.cfg)
+    torch.cuda.synchronize()
+    off = s.mem_offset + F.fdlbm_current_buffer(s.h) * fbytes
+    return _interior(s._mem[off:off + fbytes], s.cfg)
 
 
 def _copies(solver):
@@ -66,6 +83,8 @@ CASES = {
     "tube_wrap_4000x4_fp64": (lambda: W.shock_tube(nx=4000, ny=4), F.FDLBM_FP64),     # 4-row tube
     "staged32x16_262144_fp32": (lambda: W.riemann4q(n=512), F.FDLBM_FP32_STORE),    # > 200 000 sites
     "tile32x16_262144_fp64": (lambda: W.riemann4q(n=512), F.FDLBM_FP64),
+    "fneq32_reflection": (lambda: W.reflection(nx=300, ny=75), F.FDLBM_FNEQ32),
+    "fp32dw_staged_262144": (lambda: W.riemann4q(n=512), F.FDLBM_FP32_STORE_DW),
 }
 
 
@@ -77,14 +96,14 @@ def test_noalloc_matches_handle_on_two_calls(case):
     a, b = _copies(s)
     # call 1: 7 steps, result in the second buffer (odd count)
     s.step(7)
-    ref = s.get_f()
+    ref = _handle_state(s)
     assert F.fdlbm_step_noalloc(s.cfg, a, b, 7) == -1
     torch.cuda.synchronize()
     got = _interior(b, s.cfg)
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.abs(ref).max()
     # call 2: 4 more steps from that result, even count -> result stays in the first argument
     s.step(4)
-    ref = s.get_f()
+    ref = _handle_state(s)
     assert F.fdlbm_step_noalloc(s.cfg, b, a, 4) == -1
     torch.cuda.synchronize()
     got = _interior(b, s.cfg)
