@@ -205,7 +205,10 @@ int fdlbm_set_f(fdlbm_t h, const double* f);
 
 /* Checkpoint: write / read the current f (storage precision, bit exact), the
  * step count, the boundary states and the configuration to a file. fdlbm_load
- * requires a handle with the same configuration and returns FDLBM_E_IO otherwise. */
+ * requires a handle with the same configuration and returns FDLBM_E_IO otherwise.
+ * Boundary segments (fdlbm_set_boundary_segment) are not part of a checkpoint: the
+ * saved ghosts hold their values at the saved time, and the loading handle's own
+ * segments apply from its next step on. */
 int fdlbm_save(fdlbm_t h, const char* path);
 int fdlbm_load(fdlbm_t h, const char* path);
 
