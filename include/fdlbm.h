@@ -89,14 +89,27 @@ enum fdlbm_side { FDLBM_LEFT = 0, FDLBM_RIGHT = 1, FDLBM_BOTTOM = 2, FDLBM_TOP =
  *              fdlbm_get_macro returns the stored macros; fdlbm_get_f returns f_eq + g;
  *              fdlbm_set_f stores the FP64 moments of the given f and its departure from their
  *              equilibrium. Batches of FNEQ32 solves take the 32x4 or 32x8 tile variant. */
-enum fdlbm_prec { FDLBM_FP64 = 0, FDLBM_FP32_STORE = 1, FDLBM_FNEQ32 = 2, FDLBM_FP32_STORE_DW = 3 };
+enum fdlbm_prec { FDLBM_FP64 = 0, FDLBM_FP32_STORE = 1, FDLBM_FNEQ32 = 2, FDLBM_FP32_STORE_DW = 3,
+                  FDLBM_FP64_STRICT = 4 };
 /*  FP32_STORE_DW  a labelled variant of FP32_STORE ("f32-store/df32-feq"): the same storage and exact
  *              fixed-point moments finished in FP64, but the equilibrium (Eqs. 10-13: 1/T, the
  *              projections, A0, A1, F_k(theta), the per-ring constants and the 16 opposite-direction
  *              pairs) is evaluated in double-word FP32 (Dekker products, Knuth sums, compensated
  *              Horner) on the FP32 pipe instead of the FP64 one. Each f_eq is within about 2^-40 of its FP64 value before it is
  *              rounded to FP32 storage, so results differ from FP32_STORE by rare last-bit roundings.
- *              Not FP64 arithmetic; not accepted by fdlbm_batch_add. */
+ *              Not FP64 arithmetic; not accepted by fdlbm_batch_add.
+ *  FP64_STRICT FP64 storage and arithmetic in one canonical order: every value of Eqs. 3-5
+ *              (moments summed over q = 0..32 in turn), 10-13 (F_k as the quotient of Eq. 11's
+ *              polynomial by its denominator, f_eq as n F_k times its five terms added left to right)
+ *              and 17 (relaxation, then lines I-IV for x and then y) is formed one IEEE-754 FP64
+ *              operation at a time, with no fused multiply-add, no reassociation and true divisions.
+ *              Any IEEE FP64 program taking the same operations in the same order (the order is
+ *              spelled out in csrc/fdlbm_strict.cu) gets the same bits; FDLBM_FP64 agrees with it to
+ *              rounding (1e-12 relative on smooth flows). It is the slow reference-grade path: 8-9x
+ *              the FP64 path's time per step (0.10 GLUPS). One kernel pair: the tile variants do not apply
+ *              (fdlbm_set_variant is accepted and ignored; fdlbm_autotune times nothing). Not
+ *              accepted by fdlbm_batch_add or fdlbm_step_noalloc (its step needs the handle's
+ *              moment buffer). */
 
 /* Scheme variants of Sec. 4 (Fig. 2, Fig. 3): drop line II, III or IV of Eq. 17,
  * or hold the switch theta_alphaI of Eq. 16 at lambda. Default 0 = full Eq. 17. */
@@ -222,7 +235,8 @@ int fdlbm_get_variant(fdlbm_t h);               /* current variant, or a negativ
 /* Autotuner: time every variant with trial_steps launches on the current state and keep the
  * fastest. The state is not advanced: each trial launch reads the current buffer and writes the
  * other, which the next real step overwrites. times_ms (may be NULL) receives
- * fdlbm_variant_count() mean launch times in milliseconds. Synchronises the stream. */
+ * fdlbm_variant_count() mean launch times in milliseconds. Synchronises the stream.
+ * FDLBM_FP64_STRICT has one kernel pair: nothing is timed and times_ms gets zeros. */
 int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms);
 
 /* Which of the handle's two state buffers holds the current state (0: the first, at offset 0 of

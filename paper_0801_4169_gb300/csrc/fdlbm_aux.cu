@@ -42,6 +42,7 @@ cudaError_t launch_segment(int prec, void* f, const Grid& g, const Coeffs& c, co
   const int len = sg.side < 2 ? g.ny : g.nx;
   const double d = sg.side < 2 ? dy : dx;
   dim3 b(128), grid((2 * len + 127) / 128);
+  if (prec == FDLBM_FP64_STRICT) return launch_segment_strict(f, g, sg, dx, dy, s);
   if (prec == 0)
     k_segment<double><<<grid, b, 0, s>>>(static_cast<double*>(f), g, c, sg, d);
   else
@@ -52,6 +53,7 @@ cudaError_t launch_segment(int prec, void* f, const Grid& g, const Coeffs& c, co
 cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
                         unsigned* health, cudaStream_t s) {
   if (prec == FDLBM_FNEQ32) return launch_step_fneq(variant, f, fn, g, c, health, s);
+  if (prec == FDLBM_FP64_STRICT) return launch_step_strict(f, fn, g, c, health, s);  // one kernel pair
   if (prec == FDLBM_FP32_STORE_DW) return launch_step_f32dw(variant, f, fn, g, c, health, s);
   // a tile that holds a y-periodic grid's whole height reuses the interior rows' moments for its
   // ghost rows (same values, bit for bit)
@@ -73,6 +75,7 @@ cudaError_t launch_gather_health(const BatchMember* mem, int nmem, unsigned* out
 
 cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
                         const double* v, const double* T, cudaStream_t s) {
+  if (prec == FDLBM_FP64_STRICT) return launch_init_strict(f, g, rho, u, v, T, s);
   dim3 b(32, 4);
   if (prec == 0)
     k_init<double><<<grid2d(g, b), b, 0, s>>>(static_cast<double*>(f), g, c, rho, u, v, T);
@@ -83,6 +86,7 @@ cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const
 
 cudaError_t launch_dirichlet(int prec, void* f, const Grid& g, const Coeffs& c, const double bstate[4][4],
                              cudaStream_t s) {
+  if (prec == FDLBM_FP64_STRICT) return launch_dirichlet_strict(f, g, bstate, s);
   BState bs;
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) bs.s[i][j] = bstate[i][j];
@@ -97,6 +101,7 @@ cudaError_t launch_dirichlet(int prec, void* f, const Grid& g, const Coeffs& c, 
 
 cudaError_t launch_macro(int prec, const void* f, const Grid& g, double* rho, double* u, double* v, double* T,
                          cudaStream_t s) {
+  if (prec == FDLBM_FP64_STRICT) return launch_macro_strict(f, g, rho, u, v, T, s);
   dim3 b(32, 4);
   Coeffs c{};
   const double sp[4] = {1.0, 1.92, 2.99, 4.49};
@@ -113,7 +118,7 @@ cudaError_t launch_macro(int prec, const void* f, const Grid& g, double* rho, do
 
 cudaError_t launch_get_f(int prec, const void* f, const Grid& g, double* out, cudaStream_t s) {
   dim3 b(32, 4);
-  if (prec == 0)
+  if (f64_storage(prec))
     k_get_f<double><<<grid2d(g, b), b, 0, s>>>(static_cast<const double*>(f), g, out);
   else
     k_get_f<float><<<grid2d(g, b), b, 0, s>>>(static_cast<const float*>(f), g, out);
@@ -123,7 +128,7 @@ cudaError_t launch_get_f(int prec, const void* f, const Grid& g, double* out, cu
 cudaError_t launch_get_region(int prec, const void* f, const Grid& g, int x0, int y0, int w, int h, double* out,
                               cudaStream_t s) {
   dim3 b(32, 4), grid((w + 31) / 32, (h + 3) / 4);
-  if (prec == 0)
+  if (f64_storage(prec))
     k_get_region<double><<<grid, b, 0, s>>>(static_cast<const double*>(f), g, x0, y0, w, h, out);
   else
     k_get_region<float><<<grid, b, 0, s>>>(static_cast<const float*>(f), g, x0, y0, w, h, out);
@@ -132,7 +137,7 @@ cudaError_t launch_get_region(int prec, const void* f, const Grid& g, int x0, in
 
 cudaError_t launch_set_f(int prec, void* f, const Grid& g, const double* in, cudaStream_t s) {
   dim3 b(32, 4);
-  if (prec == 0)
+  if (f64_storage(prec))
     k_set_f<double><<<grid2d(g, b), b, 0, s>>>(static_cast<double*>(f), g, in);
   else
     k_set_f<float><<<grid2d(g, b), b, 0, s>>>(static_cast<float*>(f), g, in);

@@ -194,8 +194,8 @@ int fdlbm_batch_add(fdlbm_batch_t b, fdlbm_t h) {
   if (h->batch) return bfail(b, FDLBM_E_STATE, "the solve is already in a batch");
   if (!h->initialised) return bfail(b, FDLBM_E_STATE, "the solve has no state (set_macro first)");
   if (h->sticky) return bfail(b, h->sticky, "the solve carries a sticky error");
-  if (h->cfg.prec == FDLBM_FP32_STORE_DW)
-    return bfail(b, FDLBM_E_ARG, "FDLBM_FP32_STORE_DW solves are stepped alone (fdlbm_step)");
+  if (h->cfg.prec == FDLBM_FP32_STORE_DW || h->cfg.prec == FDLBM_FP64_STRICT)
+    return bfail(b, FDLBM_E_ARG, "FDLBM_FP32_STORE_DW and FDLBM_FP64_STRICT solves are stepped alone (fdlbm_step)");
   if (h->seg_on[0] || h->seg_on[1] || h->seg_on[2] || h->seg_on[3])
     return bfail(b, FDLBM_E_ARG, "a solve with boundary segments is stepped alone (fdlbm_step)");
   if (b->have_scheme && !same_scheme(b->scheme, h->cfg))

@@ -52,8 +52,8 @@ bool valid_cfg(const fdlbm_config* c, std::string* why) {
   if ((long long)c->nx * c->ny > (1LL << 31)) { *why = "nx*ny too large"; return false; }
   if (!(c->dx > 0) || !(c->dy > 0) || !(c->dt > 0) || !(c->tau > 0)) { *why = "dx, dy, dt, tau must be > 0"; return false; }
   if (!(c->lambda >= 0) || !std::isfinite(c->lambda)) { *why = "lambda must be finite and >= 0"; return false; }
-  if (c->prec < FDLBM_FP64 || c->prec > FDLBM_FP32_STORE_DW) {
-    *why = "prec must be FDLBM_FP64, FDLBM_FP32_STORE, FDLBM_FNEQ32 or FDLBM_FP32_STORE_DW";
+  if (c->prec < FDLBM_FP64 || c->prec > FDLBM_FP64_STRICT) {
+    *why = "prec must be FDLBM_FP64, FDLBM_FP32_STORE, FDLBM_FNEQ32, FDLBM_FP32_STORE_DW or FDLBM_FP64_STRICT";
     return false;
   }
   if (c->flags & ~15) { *why = "unknown flag bits"; return false; }
@@ -75,7 +75,7 @@ Layout layout_of(const fdlbm_config* c) {
   L.g.plane = (long long)L.g.pitch * L.g.rows;
   for (int s = 0; s < 4; ++s) L.g.bc[s] = c->bc[s];
   L.g.flags = c->flags;
-  L.esize = c->prec == FDLBM_FP64 ? 8 : 4;
+  L.esize = f64_storage(c->prec) ? 8 : 4;
   L.fbytes = round_up((size_t)Q * L.g.plane * L.esize, 256);
   L.g.aux_off = 0;
   if (c->prec == FDLBM_FNEQ32) {  // 33 FP32 planes of g, then 4 FP64 planes n, ux, uy, T
@@ -85,8 +85,9 @@ Layout layout_of(const fdlbm_config* c) {
   L.health_off = 2 * L.fbytes;
   L.stage_off = L.health_off + 256;
   L.mom_off = L.stage_off + round_up((size_t)4 * c->nx * c->ny * sizeof(double), 256);
-  // moment buffer of the split step: 4 FP64 planes + P in the storage precision
-  L.mom_bytes = (long long)c->nx * c->ny > 65536 && c->prec != FDLBM_FNEQ32
+  // moment buffer of the split step: 4 FP64 planes + P in the storage precision (the strict step
+  // always goes through it)
+  L.mom_bytes = ((long long)c->nx * c->ny > 65536 && c->prec != FDLBM_FNEQ32) || c->prec == FDLBM_FP64_STRICT
                     ? round_up((size_t)L.g.plane * (4 * sizeof(double) + L.esize), 256) : 0;
   L.total = L.mom_off + L.mom_bytes;
   L.g.mom = nullptr;  // set to the handle's buffer once its memory is known
@@ -160,6 +161,10 @@ Coeffs make_coeffs(const fdlbm_config* cfg) {
   }
   split(c.r, c.dr);
   split(s, c.dkS);
+  c.sdt = cfg->dt;
+  c.stau = cfg->tau;
+  c.sdr[0] = cfg->dx;
+  c.sdr[1] = cfg->dy;
   return c;
 }
 
@@ -702,6 +707,11 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
   if (!h) return fail(nullptr, FDLBM_E_ARG, "handle is NULL");
   if (trial_steps < 1) return fail(h, FDLBM_E_ARG, "trial_steps must be >= 1");
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "autotune needs a state (set_macro first)");
+  if (h->cfg.prec == FDLBM_FP64_STRICT) {  // one kernel pair: nothing to choose
+    if (times_ms)
+      for (int v = 0; v < V_COUNT; ++v) times_ms[v] = 0.f;
+    return FDLBM_OK;
+  }
   cudaEvent_t a, b;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);

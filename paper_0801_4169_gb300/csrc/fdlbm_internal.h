@@ -41,7 +41,8 @@ struct Grid {
   int bc[4];        // left, right, bottom, top
   int flags;
   // Moment buffer of the split step (V_S* variants), or null: planes n, ux, uy, T (FP64) and P
-  // (storage precision) over the padded grid, indexed like f. Only grids above 65 536 sites have one.
+  // (storage precision) over the padded grid, indexed like f. Only grids above 65 536 sites and
+  // FDLBM_FP64_STRICT solves (whose step always goes through it) have one.
   void* mom;
   // FDLBM_FNEQ32 only: byte offset, within one state buffer, of its 4 FP64 planes n, ux, uy, T
   // (after the 33 FP32 planes of g = f - f_eq); 0 for the other precisions.
@@ -77,7 +78,12 @@ struct Coeffs {
   float dv[4][2], dv2h[4][2], dv3_6[4][2], dv4_24[4][2];
   // ... and of the F_k polynomials' coefficients, dt/tau and sqrt(1/2)
   float dFh[4][4][2], dr[2], dkS[2];
+  // The raw dt, tau, dx, dy: FDLBM_FP64_STRICT forms every ratio itself, in its own order.
+  double sdt, stau, sdr[2];
 };
+
+// FP64 storage (FDLBM_FP64 and FDLBM_FP64_STRICT share the layout and the copy kernels).
+inline bool f64_storage(int prec) { return prec == FDLBM_FP64 || prec == FDLBM_FP64_STRICT; }
 
 // One member of a batch (device-resident descriptor table, sorted by tile0).
 struct BatchMember {
@@ -148,6 +154,16 @@ cudaError_t launch_macro_fneq(const void* f, const Grid& g, double* rho, double*
 cudaError_t launch_get_region_fneq(const void* f, const Grid& g, const Coeffs& c, int x0, int y0, int w, int h,
                                    double* out, cudaStream_t s);
 cudaError_t launch_set_f_fneq(void* f, const Grid& g, const Coeffs& c, const double* in, cudaStream_t s);
+// FDLBM_FP64_STRICT (fdlbm_strict.cu): the step (moments into the grid's moment buffer, then the
+// update) and the kernels that write f_eq (initial condition, Dirichlet ghosts, segments) or read
+// the moments, all in the canonical operation order.
+cudaError_t launch_step_strict(const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
+                               cudaStream_t s);
+cudaError_t launch_init_strict(void* f, const Grid& g, const double* rho, const double* u, const double* v,
+                               const double* T, cudaStream_t s);
+cudaError_t launch_dirichlet_strict(void* f, const Grid& g, const double bstate[4][4], cudaStream_t s);
+cudaError_t launch_macro_strict(const void* f, const Grid& g, double* rho, double* u, double* v, double* T,
+                                cudaStream_t s);
 cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
                         unsigned* health, cudaStream_t s);
 cudaError_t launch_init(int prec, void* f, const Grid& g, const Coeffs& c, const double* rho, const double* u,
@@ -171,6 +187,7 @@ struct Segment {
 cudaError_t launch_segment(int prec, void* f, const Grid& g, const Coeffs& c, const Segment& sg, double dx, double dy,
                            cudaStream_t s);
 cudaError_t launch_segment_fneq(void* f, const Grid& g, const Segment& sg, double dx, double dy, cudaStream_t s);
+cudaError_t launch_segment_strict(void* f, const Grid& g, const Segment& sg, double dx, double dy, cudaStream_t s);
 
 // Host helpers shared by the C ABI files (fdlbm_capi.cu).
 struct Layout {

@@ -33,6 +33,8 @@ extern "C" int fdlbm_step_noalloc(const fdlbm_config* cfg, void* f_a, void* f_b,
   if (first_bad_step) *first_bad_step = -1;
   std::string why;
   if (!valid_cfg(cfg, &why)) return fail(FDLBM_E_ARG, why);
+  if (cfg->prec == FDLBM_FP64_STRICT)
+    return fail(FDLBM_E_ARG, "FDLBM_FP64_STRICT steps through a handle's moment buffer: use fdlbm_step");
   if (!f_a || !f_b) return fail(FDLBM_E_ARG, "f_a and f_b must be device buffers");
   if ((reinterpret_cast<uintptr_t>(f_a) & 255) || (reinterpret_cast<uintptr_t>(f_b) & 255))
     return fail(FDLBM_E_ARG, "f_a and f_b must be 256-byte aligned");

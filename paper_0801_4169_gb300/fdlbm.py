@@ -18,7 +18,7 @@ FDLBM_OK, FDLBM_E_ARG, FDLBM_E_OOM, FDLBM_E_CUDA, FDLBM_E_NUMERIC, FDLBM_E_TIMEO
     0, -1, -2, -3, -4, -5, -6, -7
 FDLBM_BC_PERIODIC, FDLBM_BC_OUTFLOW, FDLBM_BC_DIRICHLET, FDLBM_BC_WALL, FDLBM_BC_HALO = 0, 1, 2, 3, 4
 FDLBM_LEFT, FDLBM_RIGHT, FDLBM_BOTTOM, FDLBM_TOP = 0, 1, 2, 3
-FDLBM_FP64, FDLBM_FP32_STORE, FDLBM_FNEQ32, FDLBM_FP32_STORE_DW = 0, 1, 2, 3
+FDLBM_FP64, FDLBM_FP32_STORE, FDLBM_FNEQ32, FDLBM_FP32_STORE_DW, FDLBM_FP64_STRICT = 0, 1, 2, 3, 4
 FDLBM_NO_LW, FDLBM_NO_DISP, FDLBM_NO_VISC, FDLBM_SWITCH_CONST = 1, 2, 4, 8
 FDLBM_HEALTH_NUMERIC, FDLBM_HEALTH_KAPPA = 1, 2
 Q = 33
