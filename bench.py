@@ -56,6 +56,11 @@ FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145, "fneq32": 927, "fp32dw": 19}
 # picks the captured variant, else null.
 TRAFFIC_B_PER_SITE = {("fp32", 2): 268.5, ("fp32", 6): 267.5, ("fp32", 11): 467.8, ("fp64", 7): 836.7,
                       ("fp64", 10): 873.5, ("fp32dw", 6): 266.3}
+# Warp instructions issued per site update (ncu smsp__inst_executed over the sites, 2048^2, same
+# kernels), by (precision, tile variant): the double-word step binds on instruction issue, whose
+# peak is 4 warp instructions per clock per SM (one per scheduler).
+WARP_INST_PER_SITE = {("fp32", 6): 121.6, ("fp32dw", 6): 131.3}
+ISSUE_PER_CLK_SM = 4.0
 DTYPE = {"fp64": "f64", "fp32": "f32-store/fixed-point+f64-moments/f64-feq",
          "fneq32": "f64-macros+f32-fneq/f64-step", "fp32dw": "f32-store/df32-feq"}
 # Variants that split a step into two launches (moment pass + update pass). Their minimum bytes per
@@ -274,6 +279,19 @@ def posed_states_leg(F, torch, prec, variant, steps=20, warmup=3):
             "status_after": status}
 
 
+def issue_roofline(prec_name, variant, site_rate, sm_mhz):
+    """Instruction issue against its peak, where ncu's warp-instruction count for the variant is
+    known (else null)."""
+    ips = WARP_INST_PER_SITE.get((prec_name, variant))
+    if ips is None:
+        return None
+    peak = ISSUE_PER_CLK_SM * N_SM * sm_mhz * 1e6 / 1e9
+    achieved = ips * site_rate / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G warp instructions/s", "frac": achieved / peak,
+            "warp_inst_per_site": ips,
+            "peak_derivation": "4 warp instructions/clk/SM x 152 SMs x %.0f MHz sampled" % sm_mhz}
+
+
 def df32_leg(F, torch, w, peaks, sm_mhz, steps=20, warmup=3):
     """The labelled double-word variant (FDLBM_FP32_STORE_DW, "f32-store/df32-feq") on the same
     workload: FP32 storage and fixed-point moments as the headline, the per-ring equilibrium
@@ -302,10 +320,12 @@ def df32_leg(F, torch, w, peaks, sm_mhz, steps=20, warmup=3):
             "tile_variant": variant, "autotune_ms": [round(t, 4) for t in times], "status": status,
             "fp64_pipe": {"achieved": fp64, "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": fp64 / fp64_peak},
             "hbm": {"achieved_gbs": hbm, "peak_gbs": peaks.get("hbm_gbs"), "frac": hbm / peaks.get("hbm_gbs", 6800.0)},
+            "issue": issue_roofline("fp32dw", variant, site_rate, sm_mhz),
             "traffic": (TRAFFIC_B_PER_SITE.get(("fp32dw", variant), 0) * w.nx * w.ny or None)
             if (w.nx, w.ny) == (4096, 4096) else None,
-            "error_vs_fp64_path": "4096^2, 2000 steps, seed 0: L1(rho) <= 1e-6 and max |d rho|/max rho <= 1e-5 "
-                                  "(tests/test_gpu_parity.py::test_fp32_storage_error_at_full_size)"}
+            "error_vs_fp64_path": "4096^2, 2000 steps, seeds 0-2: L1(rho) 1.81e-7, 4.32e-7, 8.71e-7 and "
+                                  "max |d rho|/max rho 7.3e-6, 8.6e-6, 7.5e-6 (bounds 1e-6 and 1e-5, "
+                                  "tests/test_gpu_parity.py::test_fp32_storage_error_at_full_size)"}
 
 
 def serving_leg(n_req=64, steps_scale=0.25, seed=0, budget_bytes=1 << 30):
@@ -589,7 +609,8 @@ def main():
                      "traffic": traffic, "traffic_unit": "bytes per step (ncu DRAM read + write of its launches)",
                      "peak_derivation": "2 FP64 ops/clk/SM (nominal 1.25 TFLOP/s) x 152 SMs x %.0f MHz sampled" % sm_mhz,
                      "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"), "peak_kind": peak_kind,
-                             "frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0)}},
+                             "frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0)},
+                     "issue": issue_roofline(prec_name, variant, site_rate, sm_mhz)},
         "clocks": clocks,
         "e2e": {"value": e2e_glups, "unit": "GLUPS", "h2d_bytes_per_step": macro_bytes / args.steps,
                 "d2h_bytes_per_step": macro_bytes / args.steps, "status": int(rc),

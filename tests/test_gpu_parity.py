@@ -488,16 +488,18 @@ def test_fp32_storage_l1_against_the_fp64_path(seed):
     assert np.mean(np.abs(r32 - r64)) / np.mean(np.abs(r64)) <= 1e-5
 
 
-def test_fp32_storage_error_at_full_size():
-    """The headline workload itself: the 4096^2 four-quadrant problem, seed 0, 2000 steps, FP32
-    storage (FP64 f_eq and its double-word variant) against the FP64 GPU path. L1(rho) measures
-    1.82e-7 for both and max |d rho| / max rho 6.8e-6 (FP64 f_eq) and 7.2e-6 (double word); bounds
-    1e-6 and 1e-5."""
-    w = W.riemann4q(n=4096, seed=0)
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fp32_storage_error_at_full_size(seed):
+    """The headline workload itself: the 4096^2 four-quadrant problem, seeds 0-2, 2000 steps, FP32
+    storage (FP64 f_eq and its double-word variant) against the FP64 GPU path; bounds 1e-6 on
+    L1(rho) and 1e-5 on max |d rho| / max rho. Measured, FP64 f_eq / double word:
+    L1 1.82e-7 / 1.81e-7, 4.32e-7 / 4.32e-7, 8.74e-7 / 8.71e-7;
+    max 6.8e-6 / 7.3e-6, 8.2e-6 / 8.6e-6, 7.8e-6 / 7.5e-6."""
+    w = W.riemann4q(n=4096, seed=seed)
     rho = {}
     for prec in (F.FDLBM_FP64, F.FDLBM_FP32_STORE, F.FDLBM_FP32_STORE_DW):
         s = F.Solver.from_workload(w, prec)
-        s.set_variant(10 if prec == F.FDLBM_FP64 else 2)  # the autotuner's choices at this size
+        s.set_variant(10 if prec == F.FDLBM_FP64 else 6)  # the autotuner's choices at this size
         s.step(w.steps)
         rho[prec] = s.get_macro()[0]
         assert s.sync() == 0
