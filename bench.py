@@ -55,11 +55,11 @@ FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145, "fneq32": 927, "fp32dw": 19}
 # step of this bench's 4096^2 workload (single-pass capture), divided by the sites. Reported as roofline.traffic when the autotuner
 # picks the captured variant, else null.
 TRAFFIC_B_PER_SITE = {("fp32", 2): 268.5, ("fp32", 6): 267.5, ("fp32", 11): 467.8, ("fp64", 7): 836.7,
-                      ("fp64", 10): 873.5, ("fp32dw", 6): 266.3}
+                      ("fp64", 10): 873.5, ("fp32dw", 6): 266.3, ("fp32dw", 12): 263.1}
 # Warp instructions issued per site update (ncu smsp__inst_executed over the sites, 2048^2, same
 # kernels), by (precision, tile variant): the double-word step binds on instruction issue, whose
 # peak is 4 warp instructions per clock per SM (one per scheduler).
-WARP_INST_PER_SITE = {("fp32", 6): 121.6, ("fp32dw", 6): 131.3}
+WARP_INST_PER_SITE = {("fp32", 6): 121.6, ("fp32dw", 6): 131.3, ("fp32dw", 12): 125.0}
 ISSUE_PER_CLK_SM = 4.0
 DTYPE = {"fp64": "f64", "fp32": "f32-store/fixed-point+f64-moments/f64-feq",
          "fneq32": "f64-macros+f32-fneq/f64-step", "fp32dw": "f32-store/df32-feq"}
@@ -317,7 +317,8 @@ def df32_leg(F, torch, w, peaks, sm_mhz, steps=20, warmup=3):
     fp64 = FP64_OPS_PER_LUP["fp32dw"] * site_rate / 1e9
     hbm = (BYTES_PER_LUP_SPLIT if split else BYTES_PER_LUP)["fp32dw"] * site_rate / 1e9
     return {"dtype": DTYPE["fp32dw"], "value": site_rate / 1e9, "unit": "GLUPS", "ms_per_step": ms,
-            "tile_variant": variant, "autotune_ms": [round(t, 4) for t in times], "status": status,
+            "tile_variant": variant, "kernel": "k_step_tma (tile by tensor copy)" if variant == 12 else "k_step",
+            "autotune_ms": [round(t, 4) for t in times], "status": status,
             "fp64_pipe": {"achieved": fp64, "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": fp64 / fp64_peak},
             "hbm": {"achieved_gbs": hbm, "peak_gbs": peaks.get("hbm_gbs"), "frac": hbm / peaks.get("hbm_gbs", 6800.0)},
             "issue": issue_roofline("fp32dw", variant, site_rate, sm_mhz),
@@ -603,7 +604,9 @@ def main():
                    if w.nx * w.ny * 33 * 4 > 129e6 else "inputs smaller than L2: steps read a warm cache",
                    "status": status, "parallelism": "replicas%d" % world},
         "roofline": {"bound": "alu", "kernel": "k_step_fneq (FNEQ32 step)" if prec_name == "fneq32" else
-                     "k_moments + k_update (split step)" if split else "k_step (fused step)",
+                     "k_moments + k_update (split step)" if split else
+                     "k_step_tma (fused step, tile by tensor copy)" if variant == 12 and prec_name in ("fp32", "fp32dw")
+                     else "k_step (fused step)",
                      "achieved": achieved,
                      "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak,
                      "traffic": traffic, "traffic_unit": "bytes per step (ncu DRAM read + write of its launches)",

@@ -123,7 +123,8 @@ enum fdlbm_flags {
 /* Health bits reported by fdlbm_health. */
 enum fdlbm_health_bits {
   FDLBM_HEALTH_NUMERIC = 1, /* non-finite moment, n <= 0 or T <= 0 seen (=> FDLBM_E_NUMERIC) */
-  FDLBM_HEALTH_KAPPA = 2    /* |kappa_alpha| = |u_alpha| dt/dr_alpha > 1 seen (Eq. 15); informational */
+  FDLBM_HEALTH_KAPPA = 2,   /* |kappa_alpha| = |u_alpha| dt/dr_alpha > 1 seen (Eq. 15); informational */
+  FDLBM_HEALTH_TIMEOUT = 4  /* a kernel's bounded wait for its tile copy gave up (=> FDLBM_E_TIMEOUT) */
 };
 
 /* Problem description (Eqs. 15-17 parameters). dx, dy, dt, tau > 0; lambda >= 0. */
@@ -227,7 +228,10 @@ int fdlbm_load(fdlbm_t h, const char* path);
 
 /* Launch variants of the fused step (CTA tile shapes). Every variant gives bitwise identical
  * results: a node's arithmetic does not depend on the tiling. FDLBM_FNEQ32 has its own kernel and
- * maps the variants onto its tile shapes (32x4, 32x8 at two register caps, 16x16, 64x4). */
+ * maps the variants onto its tile shapes (32x4, 32x8 at two register caps, 16x16, 64x4). The last
+ * variant (12) is, for FP32 storage, the 32x8 tile whose 36x12x33 box of f (tile, halo, all planes)
+ * arrives in shared memory by one tensor-memory-accelerator copy; other precisions run the plain
+ * 32x8 tile for it. */
 int fdlbm_variant_count(void);
 int fdlbm_set_variant(fdlbm_t h, int variant);  /* FDLBM_E_ARG if out of range */
 int fdlbm_get_variant(fdlbm_t h);               /* current variant, or a negative status */
@@ -247,6 +251,13 @@ int fdlbm_current_buffer(fdlbm_t h);
 
 /* Steps taken since the last set_macro/load (+ the loaded count). */
 long fdlbm_steps_done(fdlbm_t h);
+
+/* Self-test of the bounded wait that the tensor-copy step (variant 12) uses for its tile: one CTA
+ * on the current device initialises an mbarrier for one arrival, arrives on it (arrive != 0) or
+ * not, and waits at most iters polls. *completed = 1 and FDLBM_OK if the wait saw the arrival;
+ * *completed = 0 and FDLBM_E_TIMEOUT if it gave up (as it must without an arrival). Allocates
+ * 4 bytes of device memory; synchronous. FDLBM_E_ARG for a NULL pointer or iters < 1. */
+int fdlbm_selftest_wait(int arrive, int iters, int* completed);
 
 /* Health bits (enum fdlbm_health_bits) accumulated since set_macro; synchronises. */
 unsigned fdlbm_health(fdlbm_t h);

@@ -54,6 +54,11 @@ cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Gr
                         unsigned* health, cudaStream_t s) {
   if (prec == FDLBM_FNEQ32) return launch_step_fneq(variant, f, fn, g, c, health, s);
   if (prec == FDLBM_FP64_STRICT) return launch_step_strict(f, fn, g, c, health, s);  // one kernel pair
+  if (variant == V_TMA32x8) {
+    if (prec == FDLBM_FP32_STORE || prec == FDLBM_FP32_STORE_DW)
+      return launch_step_tma(prec == FDLBM_FP32_STORE_DW, f, fn, g, c, health, s);
+    variant = V_T32x8;  // FP64 storage: the box would take 114 KB
+  }
   if (prec == FDLBM_FP32_STORE_DW) return launch_step_f32dw(variant, f, fn, g, c, health, s);
   // a tile that holds a y-periodic grid's whole height reuses the interior rows' moments for its
   // ghost rows (same values, bit for bit)

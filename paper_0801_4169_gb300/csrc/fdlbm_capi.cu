@@ -171,6 +171,7 @@ Coeffs make_coeffs(const fdlbm_config* cfg) {
 int default_variant(const fdlbm_config* c) {
   const long long sites = (long long)c->nx * c->ny;
   if (c->prec == FDLBM_FNEQ32) return c->ny <= 4 ? V_T32x4 : V_T32x8;  // its own kernel (fdlbm_fneq.cu)
+  if (c->prec == FDLBM_FP32_STORE_DW) return V_TMA32x8;  // fastest at every size measured (tiny grids: 32 x 8)
   // Small grids are latency-bound: four lanes per node win up to a few thousand sites (400 x 4:
   // 16 us per step against 32 us for the tiles), and lose by 1.3x at 16 000 sites, where the
   // tiles have reached their latency floor while the ring-parallel launch is throughput-bound.
@@ -200,6 +201,10 @@ void poll_health(fdlbm_ctx* h, bool wait) {
   if ((h->health & H_NUMERIC) && h->sticky == FDLBM_OK) {
     h->sticky = FDLBM_E_NUMERIC;
     h->err = "a node had non-finite moments, n <= 0 or T <= 0 (step count at detection unknown; <= steps_done)";
+  }
+  if ((h->health & H_TIMEOUT) && h->sticky == FDLBM_OK) {
+    h->sticky = FDLBM_E_TIMEOUT;
+    h->err = "a tile's tensor copy did not complete within the kernel's wait limit; that step wrote nothing there";
   }
 }
 

@@ -28,7 +28,7 @@ constexpr int F_NO_LW = 1, F_NO_DISP = 2, F_NO_VISC = 4, F_SWITCH_CONST = 8;
 // Boundary kinds (same values as enum fdlbm_bc).
 constexpr int BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_DIRICHLET = 2, BC_WALL = 3, BC_HALO = 4;
 // Health bits (same values as enum fdlbm_health_bits).
-constexpr unsigned H_NUMERIC = 1u, H_KAPPA = 2u;
+constexpr unsigned H_NUMERIC = 1u, H_KAPPA = 2u, H_TIMEOUT = 4u;
 
 // Layout of one distribution buffer: SoA planes f[q][row][col] with row = j + 2, col = i + 2
 // (ghost ring of width 2 stored in place), row pitch padded to 32 elements so every row starts
@@ -112,9 +112,12 @@ inline void variant_tile(int v, int* tw, int* th) {
 // V_S* split the step in two launches: k_moments writes every node's moments once to the grid's
 // moment buffer, and the update pass stages them for its tile and ring instead of recomputing
 // them. Same functions, so the results are bitwise those of the fused variants.
+// V_TMA32x8 (FP32 storage): the 32 x 8 tile with its 36 x 12 x 33 box brought into shared memory
+// by one tensor copy (fdlbm_step_tma.cu); the other precisions run the 32 x 8 tile for it.
 enum StepVariant {
   V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_T32x32 = 5, V_T32x24 = 6,
-  V_T32x28 = 7, V_TILE_COUNT = 8, V_RP16x4 = 8, V_RP8x4 = 9, V_S32x16 = 10, V_S32x32 = 11, V_COUNT = 12
+  V_T32x28 = 7, V_TILE_COUNT = 8, V_RP16x4 = 8, V_RP8x4 = 9, V_S32x16 = 10, V_S32x32 = 11, V_TMA32x8 = 12,
+  V_COUNT = 13
 };
 inline bool variant_needs_mom(int v) { return v == V_S32x16 || v == V_S32x32; }
 
@@ -154,6 +157,9 @@ cudaError_t launch_macro_fneq(const void* f, const Grid& g, double* rho, double*
 cudaError_t launch_get_region_fneq(const void* f, const Grid& g, const Coeffs& c, int x0, int y0, int w, int h,
                                    double* out, cudaStream_t s);
 cudaError_t launch_set_f_fneq(void* f, const Grid& g, const Coeffs& c, const double* in, cudaStream_t s);
+// V_TMA32x8 for FP32 storage (fdlbm_step_tma.cu); dw: the double-word equilibrium.
+cudaError_t launch_step_tma(bool dw, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
+                            cudaStream_t s);
 // FDLBM_FP64_STRICT (fdlbm_strict.cu): the step (moments into the grid's moment buffer, then the
 // update) and the kernels that write f_eq (initial condition, Dirichlet ghosts, segments) or read
 // the moments, all in the canonical operation order.

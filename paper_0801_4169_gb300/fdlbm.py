@@ -20,7 +20,7 @@ FDLBM_BC_PERIODIC, FDLBM_BC_OUTFLOW, FDLBM_BC_DIRICHLET, FDLBM_BC_WALL, FDLBM_BC
 FDLBM_LEFT, FDLBM_RIGHT, FDLBM_BOTTOM, FDLBM_TOP = 0, 1, 2, 3
 FDLBM_FP64, FDLBM_FP32_STORE, FDLBM_FNEQ32, FDLBM_FP32_STORE_DW, FDLBM_FP64_STRICT = 0, 1, 2, 3, 4
 FDLBM_NO_LW, FDLBM_NO_DISP, FDLBM_NO_VISC, FDLBM_SWITCH_CONST = 1, 2, 4, 8
-FDLBM_HEALTH_NUMERIC, FDLBM_HEALTH_KAPPA = 1, 2
+FDLBM_HEALTH_NUMERIC, FDLBM_HEALTH_KAPPA, FDLBM_HEALTH_TIMEOUT = 1, 2, 4
 Q = 33
 
 
@@ -104,6 +104,7 @@ def lib():
             "fdlbm_last_error": (ctypes.c_char_p, [_VP]),
             "fdlbm_version": (ctypes.c_char_p, []),
             "fdlbm_step_noalloc": (ctypes.c_int, [cfgp, _VP, _VP, ctypes.c_long, ctypes.POINTER(ctypes.c_long), _VP]),
+            "fdlbm_selftest_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "fdlbm_vn_spectrum": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
             "fdlbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP]),
@@ -293,6 +294,14 @@ def fdlbm_current_buffer(h):
 
 def fdlbm_steps_done(h):
     return int(lib().fdlbm_steps_done(h))
+
+
+def fdlbm_selftest_wait(arrive, iters):
+    """(status, completed) of the bounded mbarrier wait's self-test (no exception on a timeout:
+    that is the expected outcome without an arrival)."""
+    done = ctypes.c_int(-1)
+    rc = lib().fdlbm_selftest_wait(int(arrive), int(iters), ctypes.byref(done))
+    return rc, done.value
 
 
 def fdlbm_health(h):
