@@ -585,6 +585,8 @@ def main():
     peaks, peak_kind = load_peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * sm_mhz * 1e6 / 1e9  # G ops/s at the sampled clock
+    # the same pipe measured on this GPU now: independent FMA chains at full occupancy
+    fp64_measured = F.fdlbm_fp64_rate(20000, stream) / 1e9
     site_rate = w.nx * w.ny / (per_launch_ms * 1e-3)
     achieved = FP64_OPS_PER_LUP[prec_name] * site_rate / 1e9
     split = variant in SPLIT_VARIANTS
@@ -611,6 +613,9 @@ def main():
                      "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak,
                      "traffic": traffic, "traffic_unit": "bytes per step (ncu DRAM read + write of its launches)",
                      "peak_derivation": "2 FP64 ops/clk/SM (nominal 1.25 TFLOP/s) x 152 SMs x %.0f MHz sampled" % sm_mhz,
+                     "peak_measured": fp64_measured, "frac_of_measured": achieved / fp64_measured,
+                     "peak_measured_how": "fdlbm_fp64_rate: 8 independent FMA chains per thread, 8 CTAs x 256 "
+                                          "threads per SM, CUDA events, right after the timed steps",
                      "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"), "peak_kind": peak_kind,
                              "frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0)},
                      "issue": issue_roofline(prec_name, variant, site_rate, sm_mhz)},

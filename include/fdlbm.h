@@ -252,6 +252,14 @@ int fdlbm_current_buffer(fdlbm_t h);
 /* Steps taken since the last set_macro/load (+ the loaded count). */
 long fdlbm_steps_done(fdlbm_t h);
 
+/* Diagnostic: the FP64 operation rate this GPU sustains at its present clocks, measured with one
+ * kernel of 8 CTAs of 256 threads per SM, each thread running 8 independent fused multiply-add
+ * chains for iters rounds (one FMA = one operation, the unit of the step kernels' DADD + DFMA +
+ * DMUL counts), timed with CUDA events after a warm-up launch on cuda_stream (NULL: the legacy
+ * default stream). *ops_per_s receives the rate. Synchronous; allocates 8 bytes of device
+ * memory. FDLBM_E_ARG for a NULL pointer or iters < 1. */
+int fdlbm_fp64_rate(int iters, double* ops_per_s, void* cuda_stream);
+
 /* Self-test of the bounded wait that the tensor-copy step (variant 12) uses for its tile: one CTA
  * on the current device initialises an mbarrier for one arrival, arrives on it (arrive != 0) or
  * not, and waits at most iters polls. *completed = 1 and FDLBM_OK if the wait saw the arrival;

@@ -105,6 +105,7 @@ def lib():
             "fdlbm_version": (ctypes.c_char_p, []),
             "fdlbm_step_noalloc": (ctypes.c_int, [cfgp, _VP, _VP, ctypes.c_long, ctypes.POINTER(ctypes.c_long), _VP]),
             "fdlbm_selftest_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+            "fdlbm_fp64_rate": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
             "fdlbm_vn_spectrum": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
             "fdlbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP]),
@@ -294,6 +295,15 @@ def fdlbm_current_buffer(h):
 
 def fdlbm_steps_done(h):
     return int(lib().fdlbm_steps_done(h))
+
+
+def fdlbm_fp64_rate(iters=20000, stream=None):
+    """Measured FP64 operations per second (fused multiply-add chains at full occupancy)."""
+    r = ctypes.c_double(0.0)
+    rc = lib().fdlbm_fp64_rate(int(iters), ctypes.byref(r), _stream_ptr(stream))
+    if rc != FDLBM_OK:
+        raise FdlbmError(rc, "fdlbm_fp64_rate failed")
+    return r.value
 
 
 def fdlbm_selftest_wait(arrive, iters):

@@ -190,3 +190,12 @@ def test_periodic_y_tiles_that_hold_the_whole_height(prec):
             o.set_macro(*fields)
             assert o.step(15) == 0
             assert np.max(np.abs(fr - o.get_f())) <= 1e-12 * np.abs(o.get_f()).max()
+
+
+def test_measured_fp64_rate_is_the_pipe_rate():
+    """The FP64 rate diagnostic (independent FMA chains at full occupancy) lands near the pipe's
+    2 operations per clock per SM: between 0.65 and 1.05 of 2 x 152 x the maximum SM clock
+    (clocks may sit below their maximum under the power cap)."""
+    r = F.fdlbm_fp64_rate(20000)
+    nominal = 2.0 * 152 * 2070e6
+    assert 0.65 * nominal <= r <= 1.05 * nominal, r / nominal
