@@ -144,6 +144,35 @@ def test_strict_double_mach_segments_equal_the_oracle_bit_for_bit():
     _assert_same_bits(_cross(_gpu_padded(s, w.nx, w.ny)), _cross(o.get_f_padded()), "f")
 
 
+@pytest.mark.parametrize("flags", [0, O.NO_DISP])
+def test_strict_fig3_tube_equals_the_oracle_bit_for_bit(flags):
+    """The Sec. 4 Fig. 3 tube (kappa = 1.7e4, two shocks), 3000 steps, with and without line III:
+    every bit of rho, u, v, T. The FP64 fast path is held to the oracle's rounding spread on this
+    run (its shocks amplify rounding-order differences); the strict path has no spread to hide in."""
+    w = W.riemann1d("fig3", nx=400)
+    s = F.Solver(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, STRICT, flags, w.bstate)
+    s.set_macro(*w.macros())
+    s.step(w.steps)
+    o = O.Sim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, w.bstate, flags=flags)
+    o.set_macro(*w.macros())
+    assert o.step(w.steps) == 0
+    for got, ref, fld in zip(s.get_macro(), o.get_macro(), ("rho", "u", "v", "T")):
+        _assert_same_bits(got, ref, fld)
+
+
+def test_strict_reflection_downscale_equals_the_oracle_bit_for_bit():
+    """The C3 reflection on its 300 x 75 downscale (kappa = 7.4e6 in the top state, walls, Dirichlet
+    and outflow sides), 400 steps: every f of the interior and the ghost cross."""
+    w = W.reflection(nx=300, ny=75)
+    s = F.Solver.from_workload(w, STRICT)
+    s.step(400)
+    assert _status(s) == 0
+    o = O.Sim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, w.bstate)
+    o.set_macro(*w.macros())
+    assert o.step(400) == 0
+    _assert_same_bits(_cross(_gpu_padded(s, w.nx, w.ny)), _cross(o.get_f_padded()), "f")
+
+
 def _fail_step_pair(w, max_steps):
     """Step the strict GPU path and the oracle one step at a time; f agrees bit for bit before each
     step. Returns the 1-based index of the step each side rejects (0: none within max_steps)."""
