@@ -124,7 +124,7 @@ enum fdlbm_flags {
 enum fdlbm_health_bits {
   FDLBM_HEALTH_NUMERIC = 1, /* non-finite moment, n <= 0 or T <= 0 seen (=> FDLBM_E_NUMERIC) */
   FDLBM_HEALTH_KAPPA = 2,   /* |kappa_alpha| = |u_alpha| dt/dr_alpha > 1 seen (Eq. 15); informational */
-  FDLBM_HEALTH_TIMEOUT = 4  /* a kernel's bounded wait for its tile copy gave up (=> FDLBM_E_TIMEOUT) */
+  FDLBM_HEALTH_TIMEOUT = 4  /* a kernel's bounded wait (tile copy, grid barrier) gave up (=> FDLBM_E_TIMEOUT) */
 };
 
 /* Problem description (Eqs. 15-17 parameters). dx, dy, dt, tau > 0; lambda >= 0. */
@@ -231,7 +231,12 @@ int fdlbm_load(fdlbm_t h, const char* path);
  * maps the variants onto its tile shapes (32x4, 32x8 at two register caps, 16x16, 64x4). The last
  * variant (12) is, for FP32 storage, the 32x8 tile whose 36x12x33 box of f (tile, halo, all planes)
  * arrives in shared memory by one tensor-memory-accelerator copy; other precisions run the plain
- * 32x8 tile for it. */
+ * 32x8 tile for it. Variants 13 and 14 (FP64 and FP32 storage) are persistent: one cooperative
+ * launch runs all the steps of an fdlbm_step call (up to 4096 per launch), the CTAs meeting at a
+ * grid barrier between steps, with the tile bodies of variants 9 (ring-parallel 8x4) and 2 (32x16);
+ * on small, latency-bound grids this removes the per-step launch cost. A solve with boundary
+ * segments, other precisions and fdlbm_step_noalloc run the one-step variants 9 and 2 for them. A
+ * barrier wait that gives up (bounded at about 2^22 polls) sets FDLBM_HEALTH_TIMEOUT. */
 int fdlbm_variant_count(void);
 int fdlbm_set_variant(fdlbm_t h, int variant);  /* FDLBM_E_ARG if out of range */
 int fdlbm_get_variant(fdlbm_t h);               /* current variant, or a negative status */
@@ -266,6 +271,13 @@ int fdlbm_fp64_rate(int iters, double* ops_per_s, void* cuda_stream);
  * *completed = 0 and FDLBM_E_TIMEOUT if it gave up (as it must without an arrival). Allocates
  * 4 bytes of device memory; synchronous. FDLBM_E_ARG for a NULL pointer or iters < 1. */
 int fdlbm_selftest_wait(int arrive, int iters, int* completed);
+
+/* Self-test of the grid barrier of the persistent variants: one cooperative launch of one CTA per SM
+ * meets `rounds` times at the barrier, each wait bounded by iters polls; with skip != 0 the second
+ * CTA never arrives. *completed = 1 and FDLBM_OK if every wait completed; *completed = 0 and
+ * FDLBM_E_TIMEOUT if a wait gave up (as it must with skip). Synchronous; allocates 12 bytes of device
+ * memory. FDLBM_E_ARG for a NULL pointer, iters < 1 or rounds < 1. */
+int fdlbm_selftest_grid_barrier(int skip, int iters, int rounds, int* completed);
 
 /* Health bits (enum fdlbm_health_bits) accumulated since set_macro; synchronises. */
 unsigned fdlbm_health(fdlbm_t h);

@@ -355,6 +355,7 @@ int fdlbm_create_ex(fdlbm_t* out, const fdlbm_config* cfg, void* device_mem, siz
   h->f[0] = h->mem;
   h->f[1] = h->mem + L.fbytes;
   h->d_health = reinterpret_cast<unsigned*>(h->mem + L.health_off);
+  h->d_bar = reinterpret_cast<unsigned*>(h->mem + L.health_off + 64);
   h->d_stage = reinterpret_cast<double*>(h->mem + L.stage_off);
   h->grid.mom = L.mom_bytes ? static_cast<void*>(h->mem + L.mom_off) : nullptr;
   e = cudaMallocHost(&h->h_health, sizeof(unsigned));
@@ -464,6 +465,20 @@ int fdlbm_step(fdlbm_t h, long nsteps) {
   if (!h->initialised) return fail(h, FDLBM_E_STATE, "fdlbm_step before fdlbm_set_macro / fdlbm_load");
   poll_health(h, false);
   if (h->sticky) return h->sticky;
+  if (variant_persistent(h->variant) && !any_segment(h) &&
+      (h->cfg.prec == FDLBM_FP64 || h->cfg.prec == FDLBM_FP32_STORE)) {
+    for (long done = 0; done < nsteps;) {
+      const int k = (int)(nsteps - done < kPersistMaxSteps ? nsteps - done : kPersistMaxSteps);
+      cudaError_t e = launch_steps_persist(h->cfg.prec, h->variant, h->f[h->cur], h->f[1 - h->cur], k, h->grid,
+                                           h->coeffs, h->d_health, h->d_bar, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "persistent step launch");
+      if (k & 1) h->cur = 1 - h->cur;
+      h->steps += k;
+      done += k;
+    }
+    if (nsteps > 0) return enqueue_health_copy(h);
+    return FDLBM_OK;
+  }
   for (long s = 0; s < nsteps; ++s) {
     cudaError_t e = launch_step(h->cfg.prec, h->variant, h->f[h->cur], h->f[1 - h->cur], h->grid, h->coeffs,
                                 h->d_health, h->stream);
@@ -723,9 +738,48 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
   if (e != cudaSuccess) return cuda_fail(h, e, "autotune events");
   int best = h->variant;
   float best_ms = 1e30f;
+  // The persistent variants advance the state over their trial launch: they are timed on small grids
+  // only (where they can win), from a snapshot of the current buffer and health word restored after.
+  const bool persist_ok = (h->cfg.prec == FDLBM_FP64 || h->cfg.prec == FDLBM_FP32_STORE) && !any_segment(h) &&
+                          (long long)h->cfg.nx * h->cfg.ny <= 262144;
+  unsigned char* snap = nullptr;
+  if (persist_ok) {
+    e = cudaMalloc(&snap, h->fbytes + 256);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(snap, h->f[h->cur], h->fbytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(snap + h->fbytes, h->d_health, sizeof(unsigned), cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) {
+      if (snap) cudaFree(snap);
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      return cuda_fail(h, e, "autotune snapshot");
+    }
+  }
   for (int v = 0; v < V_COUNT && e == cudaSuccess; ++v) {
-    if (variant_needs_mom(v) && !h->grid.mom) {  // not available on this grid
+    if ((variant_needs_mom(v) && !h->grid.mom) || (variant_persistent(v) && !persist_ok)) {  // not available here
       if (times_ms) times_ms[v] = 0.f;
+      continue;
+    }
+    if (variant_persistent(v)) {
+      e = launch_steps_persist(h->cfg.prec, v, h->f[h->cur], h->f[1 - h->cur], trial_steps, h->grid, h->coeffs,
+                               h->d_health, h->d_bar, h->stream);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+      if (e == cudaSuccess)
+        e = launch_steps_persist(h->cfg.prec, v, h->f[h->cur], h->f[1 - h->cur], trial_steps, h->grid, h->coeffs,
+                                 h->d_health, h->d_bar, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->f[h->cur], snap, h->fbytes, cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_health, snap + h->fbytes, sizeof(unsigned), cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      ms /= trial_steps;
+      if (times_ms) times_ms[v] = ms;
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
       continue;
     }
     // warm-up launch, then the timed ones; every launch maps f[cur] -> f[1-cur]
@@ -743,6 +797,11 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
       best_ms = ms;
       best = v;
     }
+  }
+  if (snap) {
+    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    cudaFree(snap);
+    if (e == cudaSuccess) e = e2;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -114,12 +114,19 @@ inline void variant_tile(int v, int* tw, int* th) {
 // them. Same functions, so the results are bitwise those of the fused variants.
 // V_TMA32x8 (FP32 storage): the 32 x 8 tile with its 36 x 12 x 33 box brought into shared memory
 // by one tensor copy (fdlbm_step_tma.cu); the other precisions run the 32 x 8 tile for it.
+// V_PRP8x4, V_PT32x16 (FP64 and FP32 storage): persistent -- one cooperative launch runs all the
+// steps of a call (up to kPersistMaxSteps), the CTAs meeting at a grid barrier between steps, with
+// the tile bodies of V_RP8x4 and V_T32x16 (fdlbm_step_persist.cu). One-step paths (the no-alloc
+// entry point, other precisions, solves with boundary segments) run those one-step variants.
 enum StepVariant {
   V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_T32x32 = 5, V_T32x24 = 6,
   V_T32x28 = 7, V_TILE_COUNT = 8, V_RP16x4 = 8, V_RP8x4 = 9, V_S32x16 = 10, V_S32x32 = 11, V_TMA32x8 = 12,
-  V_COUNT = 13
+  V_PRP8x4 = 13, V_PT32x16 = 14, V_COUNT = 15
 };
 inline bool variant_needs_mom(int v) { return v == V_S32x16 || v == V_S32x32; }
+inline bool variant_persistent(int v) { return v == V_PRP8x4 || v == V_PT32x16; }
+inline int variant_one_step(int v) { return v == V_PRP8x4 ? V_RP8x4 : v == V_PT32x16 ? V_T32x16 : v; }
+constexpr int kPersistMaxSteps = 4096;
 
 // Kernel launchers (fdlbm_aux.cu, fdlbm_step_f32.cu, fdlbm_step_f64.cu, fdlbm_fneq.cu). All return
 // cudaGetLastError() of the launch. prec is enum fdlbm_prec.
@@ -160,6 +167,10 @@ cudaError_t launch_set_f_fneq(void* f, const Grid& g, const Coeffs& c, const dou
 // V_TMA32x8 for FP32 storage (fdlbm_step_tma.cu); dw: the double-word equilibrium.
 cudaError_t launch_step_tma(bool dw, const void* f, void* fn, const Grid& g, const Coeffs& c, unsigned* health,
                             cudaStream_t s);
+// nsteps steps of a persistent variant in one launch (FP64 or FP32 storage): f0 -> f1 -> f0 ...,
+// the result in f1 after an odd count. bar: two zeroed-per-launch words of device memory.
+cudaError_t launch_steps_persist(int prec, int variant, void* f0, void* f1, int nsteps, const Grid& g,
+                                 const Coeffs& c, unsigned* health, unsigned* bar, cudaStream_t s);
 // FDLBM_FP64_STRICT (fdlbm_strict.cu): the step (moments into the grid's moment buffer, then the
 // update) and the kernels that write f_eq (initial condition, Dirichlet ghosts, segments) or read
 // the moments, all in the canonical operation order.
@@ -222,6 +233,7 @@ struct fdlbm_ctx {
   void* f[2] = {nullptr, nullptr};
   int cur = 0;
   unsigned* d_health = nullptr;
+  unsigned* d_bar = nullptr;   // the persistent variants' grid barrier (2 words beside the health word)
   double* d_stage = nullptr;   // 4 * nx * ny doubles for host-pointer macro calls
   double* d_fstage = nullptr;  // staging for get_f / set_f / get_f_region (allocated on first use)
   size_t fstage_cap = 0;       // doubles

@@ -40,6 +40,15 @@ constexpr double kS = 0.70710678118654752440;  // cos(pi/4)
 
 __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+// COH: a load that stays coherent with stores other CTAs made earlier in the same launch, for the
+// persistent kernels, whose steps read what the previous step wrote. It is cached in L2 only (the
+// point of coherence): an L1 line of the buffer from two steps back would be stale, and the
+// read-only path of __ldg is only valid for data that no thread of the launch writes.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldc(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }
 
@@ -264,6 +273,7 @@ __device__ __forceinline__ Mom combine_rings(double f0, const double S[4], const
   return m;
 }
 
+template <bool COH = false>
 __device__ __forceinline__ Mom node_moments(const double* __restrict__ f, long long plane, long long off,
                                             const Coeffs& c) {
   double S[4], X[4], Y[4];
@@ -271,10 +281,10 @@ __device__ __forceinline__ Mom node_moments(const double* __restrict__ f, long l
   for (int k = 0; k < 4; ++k) {
     double g[8];
 #pragma unroll
-    for (int d = 0; d < 8; ++d) g[d] = ld(f + (long long)(1 + 8 * k + d) * plane + off);
+    for (int d = 0; d < 8; ++d) g[d] = ldc<COH>(f + (long long)(1 + 8 * k + d) * plane + off);
     ring_sums(g, S[k], X[k], Y[k]);
   }
-  return combine_rings(ld(f + off), S, X, Y, c);
+  return combine_rings(ldc<COH>(f + off), S, X, Y, c);
 }
 
 // FP32 storage: the moments are summed exactly in 64-bit fixed point on the integer pipes, which
@@ -419,13 +429,14 @@ __device__ __forceinline__ Mom fix_node_moments(const float (&x)[Q], int emax) {
 // Moments of an FP32-storage node; jx, jy in hundredths and the energy in 10^-4 (to_macro<100>).
 // When the node's values are all normal and lie within 2^FIX_TOP of its largest (the usual case),
 // the terms take the short form; the results are the same.
+template <bool COH = false>
 __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long long plane, long long off,
                                             const Coeffs& c) {
   float x[Q];
   int emax = 1, emin = 255;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    x[q] = ld(f + (long long)q * plane + off);
+    x[q] = ldc<COH>(f + (long long)q * plane + off);
     const int e = (int)((__float_as_uint(x[q]) >> 23) & 0xffu);
     emax = max(emax, e);
     emin = min(emin, e);
@@ -437,12 +448,13 @@ __device__ __forceinline__ Mom node_moments(const float* __restrict__ f, long lo
 
 // One ring of a node (ring-parallel kernel, FP64 storage): S, X, Y of ring k, and f_0 (read by
 // every lane).
+template <bool COH = false>
 __device__ __forceinline__ void ring_of_node(const double* __restrict__ f, long long plane, long long off, int k,
                                              double& f0, double& S, double& X, double& Y) {
   double g[8];
 #pragma unroll
-  for (int d = 0; d < 8; ++d) g[d] = ld(f + (long long)(1 + 8 * k + d) * plane + off);
-  f0 = ld(f + off);
+  for (int d = 0; d < 8; ++d) g[d] = ldc<COH>(f + (long long)(1 + 8 * k + d) * plane + off);
+  f0 = ldc<COH>(f + off);
   ring_sums(g, S, X, Y);
 }
 
@@ -466,23 +478,26 @@ __device__ __forceinline__ Macro to_macro(const Mom& m) {
   o.P = m.n * o.T;
   return o;
 }
+template <bool COH = false>
 __device__ __forceinline__ Macro node_macro(const double* __restrict__ f, long long plane, long long off,
                                             const Coeffs& c) {
-  return to_macro<1>(node_moments(f, plane, off, c));
+  return to_macro<1>(node_moments<COH>(f, plane, off, c));
 }
+template <bool COH = false>
 __device__ __forceinline__ Macro node_macro(const float* __restrict__ f, long long plane, long long off,
                                             const Coeffs& c) {
-  return to_macro<100>(node_moments(f, plane, off, c));
+  return to_macro<100>(node_moments<COH>(f, plane, off, c));
 }
 
 // Ring-parallel kernel: the macros of the quad's node, lane r of the quad (r = 0..3) summing ring
 // r. Every lane ends with the same values, bit for bit those of node_macro. All four lanes must
 // call it together.
+template <bool COH = false>
 __device__ __forceinline__ Macro quad_macro(const double* __restrict__ f, long long plane, long long off, int r,
                                             const Coeffs& c) {
   const unsigned ALL = 0xffffffffu;
   double f0, S, X, Y;
-  ring_of_node(f, plane, off, r, f0, S, X, Y);
+  ring_of_node<COH>(f, plane, off, r, f0, S, X, Y);
   Mom m;
   // n = ((f_0 + S_0) + S_1) + (S_2 + S_3), the tree of combine_rings
   const double pn = (r == 0) ? f0 + S : S;
@@ -507,15 +522,16 @@ __device__ __forceinline__ Macro quad_macro(const double* __restrict__ f, long l
 }
 // FP32 storage: each lane forms its ring's exact sums, the quad adds the integers (exact, so in
 // any order) and exchanges the four S_k, and every lane finishes as node_moments does.
+template <bool COH = false>
 __device__ __forceinline__ Macro quad_macro(const float* __restrict__ f, long long plane, long long off, int r,
                                             const Coeffs& c) {
   const unsigned ALL = 0xffffffffu;
   float x[8];
-  const float x0 = ld(f + off);
+  const float x0 = ldc<COH>(f + off);
   int emax = f32_exp1(x0);
 #pragma unroll
   for (int d = 0; d < 8; ++d) {
-    x[d] = ld(f + (long long)(1 + 8 * r + d) * plane + off);
+    x[d] = ldc<COH>(f + (long long)(1 + 8 * r + d) * plane + off);
     emax = max(emax, f32_exp1(x[d]));
   }
   emax = max(emax, __shfl_xor_sync(ALL, emax, 1));
@@ -799,28 +815,28 @@ struct RingW {
   S nu[2];
 };
 
-template <typename S, int D>
+template <typename S, int D, bool COH = false>
 __device__ __forceinline__ S stencil_dir(const S* __restrict__ p, int pitch, const RingW<S>& w, S rfeq) {
   constexpr int XS = dir_xs(D), YS = dir_ys(D), CL = dir_cls(D), CC = dir_c2(D);
-  S acc = fma(w.w0[CC], ld(p), rfeq);
+  S acc = fma(w.w0[CC], ldc<COH>(p), rfeq);
   if (XS == 0) {
-    acc = fma(w.nu[0], ld(p + 1) + ld(p - 1), acc);
+    acc = fma(w.nu[0], ldc<COH>(p + 1) + ldc<COH>(p - 1), acc);
   } else {
     const S cp = XS > 0 ? w.P1[0][CL] : w.M1[0][CL];
     const S cm = XS > 0 ? w.M1[0][CL] : w.P1[0][CL];
-    acc = fma(cp, ld(p + 1), acc);
-    acc = fma(cm, ld(p - 1), acc);
-    const S d2 = ld(p + 2) - ld(p - 2);
+    acc = fma(cp, ldc<COH>(p + 1), acc);
+    acc = fma(cm, ldc<COH>(p - 1), acc);
+    const S d2 = ldc<COH>(p + 2) - ldc<COH>(p - 2);
     acc = XS > 0 ? fma(w.Dd[0][CL], d2, acc) : fma(-w.Dd[0][CL], d2, acc);
   }
   if (YS == 0) {
-    acc = fma(w.nu[1], ld(p + pitch) + ld(p - pitch), acc);
+    acc = fma(w.nu[1], ldc<COH>(p + pitch) + ldc<COH>(p - pitch), acc);
   } else {
     const S cp = YS > 0 ? w.P1[1][CL] : w.M1[1][CL];
     const S cm = YS > 0 ? w.M1[1][CL] : w.P1[1][CL];
-    acc = fma(cp, ld(p + pitch), acc);
-    acc = fma(cm, ld(p - pitch), acc);
-    const S d2 = ld(p + 2 * pitch) - ld(p - 2 * pitch);
+    acc = fma(cp, ldc<COH>(p + pitch), acc);
+    acc = fma(cm, ldc<COH>(p - pitch), acc);
+    const S d2 = ldc<COH>(p + 2 * pitch) - ldc<COH>(p - 2 * pitch);
     acc = YS > 0 ? fma(w.Dd[1][CL], d2, acc) : fma(-w.Dd[1][CL], d2, acc);
   }
   return acc;
@@ -853,7 +869,7 @@ struct StencilConsts<float> {
 
 // Update of all 33 velocities at one interior node, given its moments and nu_x, nu_y. ES is the
 // equilibrium's site constants: EqSite, or EqSiteDW for the double-word variant (S = float).
-template <typename S, typename ES = EqSite>
+template <typename S, typename ES = EqSite, bool COH = false>
 __device__ __forceinline__ void update_ring(int K, const S* __restrict__ f, S* __restrict__ fn, const Grid& g,
                                             const Coeffs& c, long long off, int gx, int gy, const GhostOwn& go,
                                             const ES& e, S w0base, S nux, S nuy) {
@@ -888,14 +904,14 @@ __device__ __forceinline__ void update_ring(int K, const S* __restrict__ f, S* _
     for (int d = 0; d < 8; ++d) {
       const S* p = fq + (long long)(1 + 8 * K + d) * g.plane;
       switch (d) {
-        case 0: out[0] = stencil_dir<S, 0>(p, g.pitch, w, fe[0]); break;
-        case 1: out[1] = stencil_dir<S, 1>(p, g.pitch, w, fe[1]); break;
-        case 2: out[2] = stencil_dir<S, 2>(p, g.pitch, w, fe[2]); break;
-        case 3: out[3] = stencil_dir<S, 3>(p, g.pitch, w, fe[3]); break;
-        case 4: out[4] = stencil_dir<S, 4>(p, g.pitch, w, fe[4]); break;
-        case 5: out[5] = stencil_dir<S, 5>(p, g.pitch, w, fe[5]); break;
-        case 6: out[6] = stencil_dir<S, 6>(p, g.pitch, w, fe[6]); break;
-        default: out[7] = stencil_dir<S, 7>(p, g.pitch, w, fe[7]); break;
+        case 0: out[0] = stencil_dir<S, 0, COH>(p, g.pitch, w, fe[0]); break;
+        case 1: out[1] = stencil_dir<S, 1, COH>(p, g.pitch, w, fe[1]); break;
+        case 2: out[2] = stencil_dir<S, 2, COH>(p, g.pitch, w, fe[2]); break;
+        case 3: out[3] = stencil_dir<S, 3, COH>(p, g.pitch, w, fe[3]); break;
+        case 4: out[4] = stencil_dir<S, 4, COH>(p, g.pitch, w, fe[4]); break;
+        case 5: out[5] = stencil_dir<S, 5, COH>(p, g.pitch, w, fe[5]); break;
+        case 6: out[6] = stencil_dir<S, 6, COH>(p, g.pitch, w, fe[6]); break;
+        default: out[7] = stencil_dir<S, 7, COH>(p, g.pitch, w, fe[7]); break;
       }
     }
   } else {
@@ -903,27 +919,27 @@ __device__ __forceinline__ void update_ring(int K, const S* __restrict__ f, S* _
     S fp, fm;
     // pair (d7: 0 deg, d3: 180 deg), projection p_x
     eq_pair_s<S>(er, e.p[0], e.x[0], fp, fm);
-    out[7] = stencil_dir<S, 7>(fq + (long long)(1 + 8 * K + 7) * g.plane, g.pitch, w, fp);
-    out[3] = stencil_dir<S, 3>(fq + (long long)(1 + 8 * K + 3) * g.plane, g.pitch, w, fm);
+    out[7] = stencil_dir<S, 7, COH>(fq + (long long)(1 + 8 * K + 7) * g.plane, g.pitch, w, fp);
+    out[3] = stencil_dir<S, 3, COH>(fq + (long long)(1 + 8 * K + 3) * g.plane, g.pitch, w, fm);
     // pair (d0: 45 deg, d4: 225 deg), projection s(p_x + p_y)
     eq_pair_s<S>(er, e.p[1], e.x[1], fp, fm);
-    out[0] = stencil_dir<S, 0>(fq + (long long)(1 + 8 * K + 0) * g.plane, g.pitch, w, fp);
-    out[4] = stencil_dir<S, 4>(fq + (long long)(1 + 8 * K + 4) * g.plane, g.pitch, w, fm);
+    out[0] = stencil_dir<S, 0, COH>(fq + (long long)(1 + 8 * K + 0) * g.plane, g.pitch, w, fp);
+    out[4] = stencil_dir<S, 4, COH>(fq + (long long)(1 + 8 * K + 4) * g.plane, g.pitch, w, fm);
     // pair (d1: 90 deg, d5: 270 deg), projection p_y
     eq_pair_s<S>(er, e.p[2], e.x[2], fp, fm);
-    out[1] = stencil_dir<S, 1>(fq + (long long)(1 + 8 * K + 1) * g.plane, g.pitch, w, fp);
-    out[5] = stencil_dir<S, 5>(fq + (long long)(1 + 8 * K + 5) * g.plane, g.pitch, w, fm);
+    out[1] = stencil_dir<S, 1, COH>(fq + (long long)(1 + 8 * K + 1) * g.plane, g.pitch, w, fp);
+    out[5] = stencil_dir<S, 5, COH>(fq + (long long)(1 + 8 * K + 5) * g.plane, g.pitch, w, fm);
     // pair (d2: 135 deg, d6: 315 deg), projection s(p_y - p_x)
     eq_pair_s<S>(er, e.p[3], e.x[3], fp, fm);
-    out[2] = stencil_dir<S, 2>(fq + (long long)(1 + 8 * K + 2) * g.plane, g.pitch, w, fp);
-    out[6] = stencil_dir<S, 6>(fq + (long long)(1 + 8 * K + 6) * g.plane, g.pitch, w, fm);
+    out[2] = stencil_dir<S, 2, COH>(fq + (long long)(1 + 8 * K + 2) * g.plane, g.pitch, w, fp);
+    out[6] = stencil_dir<S, 6, COH>(fq + (long long)(1 + 8 * K + 6) * g.plane, g.pitch, w, fm);
   }
   store_ring<S>(fn, g, gx, gy, go, K, out);
 }
 
 // Eq. 17 for ring K's 8 velocities at one interior node, with their r f_eq given (fe[d] for
 // direction d): the staged step's second half.
-template <typename S>
+template <typename S, bool COH = false>
 __device__ __forceinline__ void ring_stencil(int K, const S* __restrict__ f, S* __restrict__ fn, const Grid& g,
                                              const Coeffs& c, long long off, int gx, int gy, const GhostOwn& go,
                                              const S (&fe)[8], S w0base, S nux, S nuy) {
@@ -949,14 +965,14 @@ __device__ __forceinline__ void ring_stencil(int K, const S* __restrict__ f, S* 
   for (int d = 0; d < 8; ++d) {
     const S* p = fq + (long long)(1 + 8 * K + d) * g.plane;
     switch (d) {
-      case 0: out[0] = stencil_dir<S, 0>(p, g.pitch, w, fe[0]); break;
-      case 1: out[1] = stencil_dir<S, 1>(p, g.pitch, w, fe[1]); break;
-      case 2: out[2] = stencil_dir<S, 2>(p, g.pitch, w, fe[2]); break;
-      case 3: out[3] = stencil_dir<S, 3>(p, g.pitch, w, fe[3]); break;
-      case 4: out[4] = stencil_dir<S, 4>(p, g.pitch, w, fe[4]); break;
-      case 5: out[5] = stencil_dir<S, 5>(p, g.pitch, w, fe[5]); break;
-      case 6: out[6] = stencil_dir<S, 6>(p, g.pitch, w, fe[6]); break;
-      default: out[7] = stencil_dir<S, 7>(p, g.pitch, w, fe[7]); break;
+      case 0: out[0] = stencil_dir<S, 0, COH>(p, g.pitch, w, fe[0]); break;
+      case 1: out[1] = stencil_dir<S, 1, COH>(p, g.pitch, w, fe[1]); break;
+      case 2: out[2] = stencil_dir<S, 2, COH>(p, g.pitch, w, fe[2]); break;
+      case 3: out[3] = stencil_dir<S, 3, COH>(p, g.pitch, w, fe[3]); break;
+      case 4: out[4] = stencil_dir<S, 4, COH>(p, g.pitch, w, fe[4]); break;
+      case 5: out[5] = stencil_dir<S, 5, COH>(p, g.pitch, w, fe[5]); break;
+      case 6: out[6] = stencil_dir<S, 6, COH>(p, g.pitch, w, fe[6]); break;
+      default: out[7] = stencil_dir<S, 7, COH>(p, g.pitch, w, fe[7]); break;
     }
   }
   store_ring<S>(fn, g, gx, gy, go, K, out);
@@ -1060,7 +1076,7 @@ __device__ __forceinline__ void stage_feq(S* __restrict__ s_fe, int node, double
 // them again: 4-row serving tubes in 32 x 4 tiles sum 4 rows of moments instead of 6.
 // DW (S = float only): the double-word equilibrium of FDLBM_FP32_STORE_DW.
 template <typename S, int BX, int BY, int RY, bool FROM_BUF = false, bool WRAPY = false, bool STAGE = false,
-          bool DW = false>
+          bool DW = false, bool COH = false>
 __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict__ fn, const Grid& g, const Coeffs& c,
                                           unsigned* __restrict__ health, int tx, int ty, S* s_fe = nullptr) {
   static_assert(!DW || std::is_same<S, float>::value, "the double-word equilibrium is for FP32 storage");
@@ -1107,7 +1123,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
     const bool need = (inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny));
     const int cx = min(max(gx, -1), g.nx), cy = min(max(gy, -1), g.ny);  // inside the padded grid
     const long long off = (long long)(cy + NG) * g.pitch + (cx + NG);
-    const Macro m = node_macro(f, g.plane, off, c);
+    const Macro m = node_macro<COH>(f, g.plane, off, c);
     if (need) {
       if (!macro_ok(m)) bits |= H_NUMERIC;
       s_n[ly][lx] = m.n;
@@ -1174,9 +1190,9 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       const GhostOwn go = ghost_own(g, gx, gy);
       {
         const S* p = f + off;
-        S acc = fma(w0base, ld(p), s_fe[node]);
-        acc = fma(snux, ld(p + 1) + ld(p - 1), acc);
-        acc = fma(snuy, ld(p + g.pitch) + ld(p - g.pitch), acc);
+        S acc = fma(w0base, ldc<COH>(p), s_fe[node]);
+        acc = fma(snux, ldc<COH>(p + 1) + ldc<COH>(p - 1), acc);
+        acc = fma(snuy, ldc<COH>(p + g.pitch) + ldc<COH>(p - g.pitch), acc);
         store_node<S, 0>(fn, g, gx, gy, go, acc);
       }
 #pragma unroll
@@ -1184,7 +1200,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
         S fe[8];
 #pragma unroll
         for (int d = 0; d < 8; ++d) fe[d] = s_fe[(1 + 8 * K + d) * NN + node];
-        ring_stencil<S>(K, f, fn, g, c, off, gx, gy, go, fe, w0base, snux, snuy);
+        ring_stencil<S, COH>(K, f, fn, g, c, off, gx, gy, go, fe, w0base, snux, snuy);
       }
     }
   } else {
@@ -1226,15 +1242,15 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       if constexpr (DW) rfeq = e.rest;
       else rfeq = to_s<S>(e.rest);
       const S* p = f + off;
-      S acc = fma(w0base, ld(p), rfeq);
-      acc = fma(snux, ld(p + 1) + ld(p - 1), acc);
-      acc = fma(snuy, ld(p + g.pitch) + ld(p - g.pitch), acc);
+      S acc = fma(w0base, ldc<COH>(p), rfeq);
+      acc = fma(snux, ldc<COH>(p + 1) + ldc<COH>(p - 1), acc);
+      acc = fma(snuy, ldc<COH>(p + g.pitch) + ldc<COH>(p - g.pitch), acc);
       store_node<S, 0>(fn, g, gx, gy, go, acc);
     }
-    update_ring<S, ES>(0, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
-    update_ring<S, ES>(1, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
-    update_ring<S, ES>(2, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
-    update_ring<S, ES>(3, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S, ES, COH>(0, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S, ES, COH>(1, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S, ES, COH>(2, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S, ES, COH>(3, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
   }
   }
   if (bits) atomicOr(health, bits);
@@ -1302,15 +1318,17 @@ __global__ void __launch_bounds__(BX * BY, MINB) k_step_batch(const BatchMember*
 //   That costs no extra issue slots: it is one warp instruction whether one lane or four use it.
 //   Each lane then updates its own 8 velocities, and lane 0 also the rest velocity.
 // Each thread thus issues about half of k_step's FP64 chain. Results are bitwise those of k_step.
-template <typename S, int TW, int TH>
-__global__ void __launch_bounds__(4 * TW * TH) k_step_rp(const S* __restrict__ f, S* __restrict__ fn, Grid g,
-                                                       Coeffs c, unsigned* __restrict__ health) {
+// One TW x TH tile (tile_x, tile_y) of the ring-parallel step, by a CTA of 4 TW TH threads: the
+// body shared by k_step_rp (one tile per CTA) and the persistent kernel (tiles and steps in a loop).
+template <typename S, int TW, int TH, bool COH = false>
+__device__ __forceinline__ void rp_tile(const S* __restrict__ f, S* __restrict__ fn, const Grid& g, const Coeffs& c,
+                                        unsigned* __restrict__ health, int tile_x, int tile_y) {
   constexpr int SW = TW + 2, SH = TH + 2, NQ = TW * TH;
   using SC = StencilConsts<S>;
   __shared__ double s_n[SH][SW], s_ux[SH][SW], s_uy[SH][SW], s_T[SH][SW];
   __shared__ S s_P[SH][SW];
   const int r = threadIdx.x & 3, quad = threadIdx.x >> 2;
-  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+  const int x0 = tile_x * TW, y0 = tile_y * TH;
   unsigned bits = 0;
 
   // Phase 1: moments on the tile and its ring; every lane takes part in every shuffle.
@@ -1326,7 +1344,7 @@ __global__ void __launch_bounds__(4 * TW * TH) k_step_rp(const S* __restrict__ f
         inslot && ((inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny)));
     const int cx = min(max(gx, -1), g.nx), cy = min(max(gy, -1), g.ny);
     const long long off = (long long)(cy + NG) * g.pitch + (cx + NG);
-    const Macro mm = quad_macro(f, g.plane, off, r, c);
+    const Macro mm = quad_macro<COH>(f, g.plane, off, r, c);
     if (need && r == 0) {
       if (!macro_ok(mm)) bits |= H_NUMERIC;
       s_n[ly][lx] = mm.n;
@@ -1368,14 +1386,19 @@ __global__ void __launch_bounds__(4 * TW * TH) k_step_rp(const S* __restrict__ f
     if (r == 0) {
       const S rfeq = to_s<S>(e.rest);
       const S* p = f + off;
-      S acc = fma(w0base, ld(p), rfeq);
-      acc = fma(snux, ld(p + 1) + ld(p - 1), acc);
-      acc = fma(snuy, ld(p + g.pitch) + ld(p - g.pitch), acc);
+      S acc = fma(w0base, ldc<COH>(p), rfeq);
+      acc = fma(snux, ldc<COH>(p + 1) + ldc<COH>(p - 1), acc);
+      acc = fma(snuy, ldc<COH>(p + g.pitch) + ldc<COH>(p - g.pitch), acc);
       store_node<S, 0>(fn, g, gx, gy, go, acc);
     }
-    update_ring<S>(r, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
+    update_ring<S, EqSite, COH>(r, f, fn, g, c, off, gx, gy, go, e, w0base, snux, snuy);
   }
   if (bits) atomicOr(health, bits);
+}
+template <typename S, int TW, int TH>
+__global__ void __launch_bounds__(4 * TW * TH) k_step_rp(const S* __restrict__ f, S* __restrict__ fn, Grid g,
+                                                       Coeffs c, unsigned* __restrict__ health) {
+  rp_tile<S, TW, TH>(f, fn, g, c, health, blockIdx.x, blockIdx.y);
 }
 
 // health words of the members into one array (one device-to-host copy per batch round)

@@ -106,6 +106,7 @@ def lib():
             "fdlbm_step_noalloc": (ctypes.c_int, [cfgp, _VP, _VP, ctypes.c_long, ctypes.POINTER(ctypes.c_long), _VP]),
             "fdlbm_selftest_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "fdlbm_fp64_rate": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
+            "fdlbm_selftest_grid_barrier": (ctypes.c_int, [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int)]),
             "fdlbm_vn_spectrum": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
             "fdlbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP]),
@@ -304,6 +305,13 @@ def fdlbm_fp64_rate(iters=20000, stream=None):
     if rc != FDLBM_OK:
         raise FdlbmError(rc, "fdlbm_fp64_rate failed")
     return r.value
+
+
+def fdlbm_selftest_grid_barrier(skip, iters, rounds=4):
+    """(status, completed) of the persistent variants' grid-barrier self-test."""
+    done = ctypes.c_int(-1)
+    rc = lib().fdlbm_selftest_grid_barrier(int(skip), int(iters), int(rounds), ctypes.byref(done))
+    return rc, done.value
 
 
 def fdlbm_selftest_wait(arrive, iters):
