@@ -66,6 +66,8 @@ DTYPE = {"fp64": "f64", "fp32": "f32-store/fixed-point+f64-moments/f64-feq",
 # Variants that split a step into two launches (moment pass + update pass). Their minimum bytes per
 # site update: f read twice and written once, the moment buffer (4 FP64 + P) written and read.
 SPLIT_VARIANTS = (10, 11)
+# Variants that run all the steps of a call in one cooperative launch (up to 4096 steps each).
+PERSISTENT_VARIANTS = (13, 14)
 BYTES_PER_LUP_SPLIT = {"fp64": 3 * 33 * 8 + 2 * (4 * 8 + 8), "fp32": 3 * 33 * 4 + 2 * (4 * 8 + 4),
                        "fp32dw": 3 * 33 * 4 + 2 * (4 * 8 + 4)}
 # Minimum HBM bytes per site update: read and write all 33 f once.
@@ -608,7 +610,8 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_step_fneq (FNEQ32 step)" if prec_name == "fneq32" else
                      "k_moments + k_update (split step)" if split else
                      "k_step_tma (fused step, tile by tensor copy)" if variant == 12 and prec_name in ("fp32", "fp32dw")
-                     else "k_step (fused step)",
+                     else "k_persist_rp / k_persist_tile (persistent steps)" if variant in PERSISTENT_VARIANTS
+                     and prec_name in ("fp32", "fp64") else "k_step (fused step)",
                      "achieved": achieved,
                      "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak,
                      "traffic": traffic, "traffic_unit": "bytes per step (ncu DRAM read + write of its launches)",
@@ -625,7 +628,8 @@ def main():
                 "note": "one solve per timed region: set_macro (H2D) + %d steps + get_macro (D2H)" % args.steps,
                 "parts_ms": {"set_macro": round((t1 - t0) * 1e3, 2), "steps": round((t2 - t1) * 1e3, 2),
                              "get_macro": round((t3 - t2) * 1e3, 2)}},
-        "gpu_launches": args.steps * (2 if split else 1),
+        "gpu_launches": -(-args.steps // 4096) if variant in PERSISTENT_VARIANTS and prec_name in ("fp32", "fp64")
+        else args.steps * (2 if split else 1),
     }
     solver.close()
     if rank == 0 and world == 1 and args.workload == "riemann4096" and not args.small and args.n is None:
