@@ -1149,8 +1149,8 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
   __syncthreads();
 
   if constexpr (STAGE) {
-    // Staged phase 2: first every node's 33 r f_eq (the FP64 work) into shared memory, s_fe[q][node],
-    // then the stencils (FP32 and memory work) from there.
+    // Staged phase 2: first the thread's nodes' 33 r f_eq each (the FP64 work) into shared memory,
+    // s_fe[q][node], then their stencils (FP32 and memory work) from there.
     constexpr int NN = TW * TH;
 #pragma unroll 1
     for (int rr = 0; rr < RY; ++rr) {
@@ -1160,7 +1160,8 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
       const int node = (threadIdx.y + rr * BY) * TW + threadIdx.x;
       stage_feq<S, NN, DW>(s_fe, node, s_n[ly][lx], s_ux[ly][lx], s_uy[ly][lx], s_T[ly][lx], c);
     }
-    __syncthreads();
+    // no barrier: a thread reads back only its own nodes' f_eq (a node's stencil takes r f_eq at
+    // the node itself), so its warps run on into their stencils as soon as they are done
 #pragma unroll 1
     for (int rr = 0; rr < RY; ++rr) {
       const int lx = threadIdx.x + 1, ly = threadIdx.y + rr * BY + 1;
