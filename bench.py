@@ -281,6 +281,26 @@ def posed_states_leg(F, torch, prec, variant, steps=20, warmup=3):
             "status_after": status}
 
 
+def host_copy_rates(torch, h_src, h_dst):
+    """This box's pinned host <-> device copy rates (GB/s, best of 3 copies of one macro array),
+    taken before the end-to-end pass: the e2e figure's copies run at these rates, which differ
+    between machines several-fold."""
+    d = torch.empty(h_src.shape, dtype=h_src.dtype, device="cuda")
+    nbytes = h_src.numel() * h_src.element_size()
+    out = {}
+    for name, dst, src in (("h2d", d, h_src), ("d2h", h_dst, d)):
+        best = float("inf")
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t)
+        out[name] = round(nbytes / best / 1e9, 1)
+    del d
+    return out
+
+
 def issue_roofline(prec_name, variant, site_rate, sm_mhz):
     """Instruction issue against its peak, where ncu's warp-instruction count for the variant is
     known (else null)."""
@@ -530,10 +550,11 @@ def main():
     stream = torch.cuda.Stream()
     solver = F.Solver(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.lam, w.bc, prec, 0, w.bstate, stream=stream)
     # pinned host copies of the inputs (for the end-to-end leg)
-    pinned = []
+    pinned, pinned_t = [], []
     for a in w.macros():
         t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
         t.numpy()[...] = a
+        pinned_t.append(t)
         pinned.append(t.numpy())
     solver.set_macro(*pinned)
     if args.variant is None:
@@ -571,7 +592,9 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    h_out = [torch.empty(a.shape, dtype=torch.float64, pin_memory=True).numpy() for a in w.macros()]
+    h_out_t = [torch.empty(a.shape, dtype=torch.float64, pin_memory=True) for a in w.macros()]
+    h_out = [t.numpy() for t in h_out_t]
+    host_copy = host_copy_rates(torch, pinned_t[0], h_out_t[0])
     t0 = time.perf_counter()
     solver.set_macro(*pinned)                      # synchronous: H2D copies and f = f_eq
     t1 = time.perf_counter()
@@ -627,7 +650,8 @@ def main():
                 "d2h_bytes_per_step": macro_bytes / args.steps, "status": int(rc),
                 "note": "one solve per timed region: set_macro (H2D) + %d steps + get_macro (D2H)" % args.steps,
                 "parts_ms": {"set_macro": round((t1 - t0) * 1e3, 2), "steps": round((t2 - t1) * 1e3, 2),
-                             "get_macro": round((t3 - t2) * 1e3, 2)}},
+                             "get_macro": round((t3 - t2) * 1e3, 2)},
+                "host_copy_gbs": host_copy},
         "gpu_launches": -(-args.steps // 4096) if variant in PERSISTENT_VARIANTS and prec_name in ("fp32", "fp64")
         else args.steps * (2 if split else 1),
     }
