@@ -324,14 +324,19 @@ def test_full_size_sampled_one_step_parity(name, prec):
     assert s.sync() == 0
 
 
-@pytest.mark.parametrize("prec", [F.FDLBM_FP32_STORE, F.FDLBM_FP64])
-def test_beyond_2e31_elements_per_buffer(prec):
+@pytest.mark.parametrize("prec,variant", [(F.FDLBM_FP32_STORE, None), (F.FDLBM_FP64, None),
+                                          (F.FDLBM_FP32_STORE_DW, None), (F.FDLBM_FP32_STORE, 12)])
+def test_beyond_2e31_elements_per_buffer(prec, variant):
     """8192^2 nodes: each buffer holds 33 x 8196 x 8224 = 2.2e9 elements, beyond 2^31, so every
     plane offset past the 31st velocity and every flat index above 2^31 takes the 64-bit path
-    (17.8 GB with FP32 storage, 35.6 GB with FP64). One step from the initial state agrees with
-    the oracle's update of sampled nodes: the four corners, the last row and column, random nodes."""
+    (17.8 GB with FP32 storage, 35.6 GB with FP64). The double-word precision's default and
+    variant 12 run the tile by tensor copy, whose box reaches planes 2.2 GB apart. One step from
+    the initial state agrees with the oracle's update of sampled nodes: the four corners, the last
+    row and column, random nodes."""
     w = W.riemann4q(n=8192, steps=1)
     s = F.Solver.from_workload(w, prec)
+    if variant is not None:
+        s.set_variant(variant)
     n = w.nx
     rng = np.random.default_rng(11)
     nodes = [(2, 2), (n - 3, 2), (2, n - 3), (n - 3, n - 3), (n // 2, n - 3), (n - 3, n // 2)]
