@@ -479,7 +479,7 @@ def test_fp32_storage_velocity_and_temperature_are_within_ulps_of_the_exact_mome
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_fp32_storage_l1_against_the_fp64_path(seed):
-    """The four-quadrant recipe of the C5 workload at 512^2, 2000 steps: FP32 storage against the
+    """The 4096^2 four-quadrant recipe at 512^2, 2000 steps: FP32 storage against the
     FP64 GPU path, L1(rho) relative <= 1e-5 (the target stated for Mach <= 5 states). At 4096^2 the
     three seeds measure 1.8e-7 to 8.7e-7."""
     w = W.riemann4q(n=512, seed=seed)
@@ -517,7 +517,7 @@ def test_fp32_storage_error_at_full_size(seed):
 
 
 def test_reflection_downscale_matches_oracle_within_its_rounding_spread():
-    """The C3 reflection on its 300 x 75 downscale, FP64, 400 steps: GPU and oracle moments agree to
+    """The regular reflection (Sec. 5.2.1) on its 300 x 75 downscale, FP64, 400 steps: GPU and oracle moments agree to
     3x the oracle's own spread under 4-ulp per-step perturbations of f (kappa = 7.4e6 in the top
     state, and the switch amplifies rounding-order differences at the shocks). After 1000 steps the
     GPU differs by 8.4e-7 (rho), 1.6e-6 (v) relative to the field maxima."""

@@ -161,7 +161,7 @@ def test_strict_fig3_tube_equals_the_oracle_bit_for_bit(flags):
 
 
 def test_strict_reflection_downscale_equals_the_oracle_bit_for_bit():
-    """The C3 reflection on its 300 x 75 downscale (kappa = 7.4e6 in the top state, walls, Dirichlet
+    """The regular reflection (Sec. 5.2.1) on its 300 x 75 downscale (kappa = 7.4e6 in the top state, walls, Dirichlet
     and outflow sides), 400 steps: every f of the interior and the ghost cross."""
     w = W.reflection(nx=300, ny=75)
     s = F.Solver.from_workload(w, STRICT)

@@ -177,7 +177,7 @@ def _c5(seed, lam):
 
 
 @pytest.mark.parametrize("lam,expect", [(1.0, (2, 3, 4)), (3.0, (2, 5, 0)), (20.0, (2, 9, 0))])
-def test_c5_baseline_ranges_scan(lam, expect):
+def test_four_quadrant_posed_ranges_scan(lam, expect):
     """The FP64 oracle on those ranges, seeds 0-2: at lambda = 1 every seed is rejected within 4 steps; from lambda = 3 to 20 seed 2 runs 2000 steps while
     seeds 0 and 1 are rejected within 9. (0 = all 2000 steps ran.)"""
     got = tuple(_fail_step(_c5(seed, lam), 2000 if e == 0 else 20) for seed, e in enumerate(expect))
@@ -185,7 +185,7 @@ def test_c5_baseline_ranges_scan(lam, expect):
 
 
 @pytest.mark.parametrize("seed,lam,steps", [(0, 1.0, 1), (1, 1.0, 2)])
-def test_c5_baseline_failures_hold_in_exact_arithmetic(seed, lam, steps):
+def test_four_quadrant_posed_failures_hold_in_exact_arithmetic(seed, lam, steps):
     """The node that fails first (a quadrant interface) has T < 0 at 40 digits too, agreeing with
     FP64 to 1e-6: these ranges are rejected by the scheme."""
     T64, Tmp = _decide(_c5(seed, lam), steps)
@@ -193,7 +193,7 @@ def test_c5_baseline_failures_hold_in_exact_arithmetic(seed, lam, steps):
     assert abs(T64 - float(Tmp)) <= 1e-6 * abs(float(Tmp))
 
 
-def test_c3_sharp_shock_needs_strong_viscosity():
+def test_reflection_sharp_shock_needs_strong_viscosity():
     """The regular reflection (Sec. 5.2.1, Eq. 26) on the 300 x 75 downscale (dx = 4e-3, dt = tau = 1e-5), started from a sharp
     30-degree incident shock through the top-left corner: rejected within 4 steps at lambda = 1 and 5,
     while at lambda = 20, the value the 1200 x 300 run uses, it runs (200 steps here; 4000 in a longer scan)."""
@@ -203,7 +203,7 @@ def test_c3_sharp_shock_needs_strong_viscosity():
     assert _fail_step(W.reflection(nx=300, ny=75, init="shock", lam=20.0), 200) == 0
 
 
-def test_c3_sharp_shock_failure_holds_in_exact_arithmetic():
+def test_reflection_sharp_shock_failure_holds_in_exact_arithmetic():
     """At lambda = 1 the first bad node (next to the wall, behind the incident shock) has T < 0 after
     3 steps at 40 digits too; FP64 is off by 4e-6 relative there (kappa ~ 7e6 in the top state)."""
     T64, Tmp = _decide(W.reflection(nx=300, ny=75, init="shock", lam=1.0), 3)
@@ -211,7 +211,7 @@ def test_c3_sharp_shock_failure_holds_in_exact_arithmetic():
     assert abs(T64 - float(Tmp)) <= 2e-5 * abs(float(Tmp))
 
 
-def test_c3_time_step_of_the_config_fails():
+def test_reflection_time_step_1e5_at_dx_1e3_fails():
     """dt = 1e-5 at dx = 1e-3 (kappa_x = 0.2 in the Mach-20 stream), the pair first posed for it, on a 120 x 40
     window of the reflection at that spacing: rejected within 100 steps from the post-shock start
     (lambda 1 and 20) and within 2 from the sharp shock. With dt = tau = 2.5e-6 the same problem
