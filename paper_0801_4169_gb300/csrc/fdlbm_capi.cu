@@ -798,8 +798,11 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
       best = v;
     }
   }
-  if (snap) {
-    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  if (snap) {  // whatever happened above, the state goes back to the snapshot
+    cudaError_t e2 = cudaMemcpyAsync(h->f[h->cur], snap, h->fbytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e2 == cudaSuccess)
+      e2 = cudaMemcpyAsync(h->d_health, snap + h->fbytes, sizeof(unsigned), cudaMemcpyDeviceToDevice, h->stream);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->stream);
     cudaFree(snap);
     if (e == cudaSuccess) e = e2;
   }
