@@ -228,8 +228,8 @@ int fdlbm_load(fdlbm_t h, const char* path);
 
 /* Launch variants of the fused step (CTA tile shapes). Every variant gives bitwise identical
  * results: a node's arithmetic does not depend on the tiling. FDLBM_FNEQ32 has its own kernel and
- * maps the variants onto its tile shapes (32x4, 32x8 at two register caps, 16x16, 64x4). The last
- * variant (12) is, for FP32 storage, the 32x8 tile whose 36x12x33 box of f (tile, halo, all planes)
+ * maps the variants onto its tile shapes (32x4, 32x8 at two register caps, 16x16, 64x4). Variant
+ * 12 is, for FP32 storage, the 32x8 tile whose 36x12x33 box of f (tile, halo, all planes)
  * arrives in shared memory by one tensor-memory-accelerator copy; other precisions run the plain
  * 32x8 tile for it. Variants 13 and 14 (FP64 and FP32 storage) are persistent: one cooperative
  * launch runs all the steps of an fdlbm_step call (up to 4096 per launch), the CTAs meeting at a
