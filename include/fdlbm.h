@@ -233,8 +233,9 @@ int fdlbm_load(fdlbm_t h, const char* path);
  * arrives in shared memory by one tensor-memory-accelerator copy; other precisions run the plain
  * 32x8 tile for it. Variants 13 and 14 (FP64 and FP32 storage) are persistent: one cooperative
  * launch runs all the steps of an fdlbm_step call (up to 4096 per launch), the CTAs meeting at a
- * grid barrier between steps, with the tile bodies of variants 9 (ring-parallel 8x4) and 2 (32x16);
- * on small, latency-bound grids this removes the per-step launch cost. A solve with boundary
+ * grid barrier between steps, with the tile bodies of variants 9 (ring-parallel 8x4) and 2 (32x16).
+ * That removes the per-step launch cost, 3% of a 1600-site step (small grids wait on the FP64 pipe
+ * of their few warps, not on launches); the autotuner times them on small grids. A solve with boundary
  * segments, other precisions and fdlbm_step_noalloc run the one-step variants 9 and 2 for them. A
  * barrier wait that gives up (bounded at about 2^22 polls) sets FDLBM_HEALTH_TIMEOUT. */
 int fdlbm_variant_count(void);
