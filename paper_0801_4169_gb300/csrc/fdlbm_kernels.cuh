@@ -1071,6 +1071,96 @@ __device__ __forceinline__ void stage_feq(S* __restrict__ s_fe, int node, double
   }
 }
 
+// One node of phase 1: the moments of local node (lx, ly) of the tile whose first node is (x0, y0)
+// (local (1, 1)), stored if an update needs them: every interior node and the ghost layer next to
+// an edge, never a grid corner. Its loads take an address clamped into the padded grid, so that a
+// caller can run it branch-free on slots it does not need.
+template <typename S, int SW, bool COH>
+__device__ __forceinline__ void moment_slot(const S* __restrict__ f, const Grid& g, const Coeffs& c, int x0, int y0,
+                                            int lx, int ly, double (*s_n)[SW], double (*s_ux)[SW],
+                                            double (*s_uy)[SW], double (*s_T)[SW], S (*s_P)[SW], unsigned& bits) {
+  const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+  const bool inx = gx >= 0 && gx < g.nx, iny = gy >= 0 && gy < g.ny;
+  const bool need = (inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny));
+  const int cx = min(max(gx, -1), g.nx), cy = min(max(gy, -1), g.ny);  // inside the padded grid
+  const long long off = (long long)(cy + NG) * g.pitch + (cx + NG);
+  const Macro m = node_macro<COH>(f, g.plane, off, c);
+  if (need) {
+    if (!macro_ok(m)) bits |= H_NUMERIC;
+    s_n[ly][lx] = m.n;
+    s_ux[ly][lx] = m.ux;
+    s_uy[ly][lx] = m.uy;
+    s_T[ly][lx] = m.T;
+    s_P[ly][lx] = from_d<S>(m.P);
+  }
+}
+
+// Staged phase 2 of a BX x (BY RY) tile (FP32 storage), from the moments of the tile and its ring
+// in shared memory: first the thread's nodes' 33 r f_eq each (the FP64 work) into s_fe[q][node],
+// then their stencils (FP32 and memory work) from there.
+template <typename S, int BX, int BY, int RY, int SW, bool DW, bool COH>
+__device__ __forceinline__ void staged_update(const S* __restrict__ f, S* __restrict__ fn, const Grid& g,
+                                              const Coeffs& c, int x0, int y0, const double (*s_n)[SW],
+                                              const double (*s_ux)[SW], const double (*s_uy)[SW],
+                                              const double (*s_T)[SW], const S (*s_P)[SW], S* __restrict__ s_fe,
+                                              unsigned& bits) {
+  constexpr int TW = BX, TH = BY * RY;
+  using SC = StencilConsts<S>;
+  constexpr int NN = TW * TH;
+#pragma unroll 1
+  for (int rr = 0; rr < RY; ++rr) {
+    const int lx = threadIdx.x + 1, ly = threadIdx.y + rr * BY + 1;
+    const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + rr * BY;
+    if (gx >= g.nx || gy >= g.ny) continue;
+    const int node = (threadIdx.y + rr * BY) * TW + threadIdx.x;
+    stage_feq<S, NN, DW>(s_fe, node, s_n[ly][lx], s_ux[ly][lx], s_uy[ly][lx], s_T[ly][lx], c);
+  }
+  // no barrier: a thread reads back only its own nodes' f_eq (a node's stencil takes r f_eq at
+  // the node itself), so its warps run on into their stencils as soon as they are done
+#pragma unroll 1
+  for (int rr = 0; rr < RY; ++rr) {
+    const int lx = threadIdx.x + 1, ly = threadIdx.y + rr * BY + 1;
+    const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + rr * BY;
+    if (gx >= g.nx || gy >= g.ny) continue;
+    const int node = (threadIdx.y + rr * BY) * TW + threadIdx.x;
+    const double ux = s_ux[ly][lx], uy = s_uy[ly][lx];
+    S thx, thy;
+    if (g.flags & F_SWITCH_CONST) {
+      thx = SC::lam(c);
+      thy = SC::lam(c);
+    } else {
+      const S P0 = s_P[ly][lx];
+      const S sx = s_P[ly][lx + 1] + s_P[ly][lx - 1], sy = s_P[ly + 1][lx] + s_P[ly - 1][lx];
+      thx = SC::lam(c) * fabs(fma((S)-2, P0, sx) * recip(fma((S)2, P0, sx)));
+      thy = SC::lam(c) * fabs(fma((S)-2, P0, sy) * recip(fma((S)2, P0, sy)));
+    }
+    const S akx = fabs(from_d<S>(ux) * SC::kx(c)), aky = fabs(from_d<S>(uy) * SC::ky(c));
+    if (akx > (S)1 || aky > (S)1) bits |= H_KAPPA;
+    S snux = 0, snuy = 0;
+    if (!(g.flags & F_NO_VISC)) {
+      snux = (S)0.5 * thx * akx * ((S)1 - akx);
+      snuy = (S)0.5 * thy * aky * ((S)1 - aky);
+    }
+    const S w0base = ((S)1 - SC::r(c)) - (S)2 * (snux + snuy);
+    const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
+    const GhostOwn go = ghost_own(g, gx, gy);
+    {
+      const S* p = f + off;
+      S acc = fma(w0base, ldc<COH>(p), s_fe[node]);
+      acc = fma(snux, ldc<COH>(p + 1) + ldc<COH>(p - 1), acc);
+      acc = fma(snuy, ldc<COH>(p + g.pitch) + ldc<COH>(p - g.pitch), acc);
+      store_node<S, 0>(fn, g, gx, gy, go, acc);
+    }
+#pragma unroll
+    for (int K = 0; K < 4; ++K) {
+      S fe[8];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) fe[d] = s_fe[(1 + 8 * K + d) * NN + node];
+      ring_stencil<S, COH>(K, f, fn, g, c, off, gx, gy, go, fe, w0base, snux, snuy);
+    }
+  }
+}
+
 // WRAPY (batched kernel): a tile that holds a y-periodic grid's whole height takes its two ghost
 // rows' moments from the interior rows they copy (bit for bit the same values) instead of summing
 // them again: 4-row serving tubes in 32 x 4 tiles sum 4 rows of moments instead of 6.
@@ -1117,21 +1207,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
     const int idx = tid + k * NT;
     // the slots before the last always lie in the tile ring (no branch); the last one is guarded
     if (WRAPY ? idx >= nslot : ((k + 1) * NT > SW * SH && idx >= SW * SH)) continue;
-    const int lx = idx % SW, ly = idx / SW + (wrap ? 1 : 0);
-    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-    const bool inx = gx >= 0 && gx < g.nx, iny = gy >= 0 && gy < g.ny;
-    const bool need = (inx && iny) || (iny && (gx == -1 || gx == g.nx)) || (inx && (gy == -1 || gy == g.ny));
-    const int cx = min(max(gx, -1), g.nx), cy = min(max(gy, -1), g.ny);  // inside the padded grid
-    const long long off = (long long)(cy + NG) * g.pitch + (cx + NG);
-    const Macro m = node_macro<COH>(f, g.plane, off, c);
-    if (need) {
-      if (!macro_ok(m)) bits |= H_NUMERIC;
-      s_n[ly][lx] = m.n;
-      s_ux[ly][lx] = m.ux;
-      s_uy[ly][lx] = m.uy;
-      s_T[ly][lx] = m.T;
-      s_P[ly][lx] = from_d<S>(m.P);
-    }
+    moment_slot<S, SW, COH>(f, g, c, x0, y0, idx % SW, idx / SW + (wrap ? 1 : 0), s_n, s_ux, s_uy, s_T, s_P, bits);
   }
   if (wrap) {  // CTA-uniform
     __syncthreads();
@@ -1149,61 +1225,7 @@ __device__ __forceinline__ void step_tile(const S* __restrict__ f, S* __restrict
   __syncthreads();
 
   if constexpr (STAGE) {
-    // Staged phase 2: first the thread's nodes' 33 r f_eq each (the FP64 work) into shared memory,
-    // s_fe[q][node], then their stencils (FP32 and memory work) from there.
-    constexpr int NN = TW * TH;
-#pragma unroll 1
-    for (int rr = 0; rr < RY; ++rr) {
-      const int lx = threadIdx.x + 1, ly = threadIdx.y + rr * BY + 1;
-      const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + rr * BY;
-      if (gx >= g.nx || gy >= g.ny) continue;
-      const int node = (threadIdx.y + rr * BY) * TW + threadIdx.x;
-      stage_feq<S, NN, DW>(s_fe, node, s_n[ly][lx], s_ux[ly][lx], s_uy[ly][lx], s_T[ly][lx], c);
-    }
-    // no barrier: a thread reads back only its own nodes' f_eq (a node's stencil takes r f_eq at
-    // the node itself), so its warps run on into their stencils as soon as they are done
-#pragma unroll 1
-    for (int rr = 0; rr < RY; ++rr) {
-      const int lx = threadIdx.x + 1, ly = threadIdx.y + rr * BY + 1;
-      const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + rr * BY;
-      if (gx >= g.nx || gy >= g.ny) continue;
-      const int node = (threadIdx.y + rr * BY) * TW + threadIdx.x;
-      const double ux = s_ux[ly][lx], uy = s_uy[ly][lx];
-      S thx, thy;
-      if (g.flags & F_SWITCH_CONST) {
-        thx = SC::lam(c);
-        thy = SC::lam(c);
-      } else {
-        const S P0 = s_P[ly][lx];
-        const S sx = s_P[ly][lx + 1] + s_P[ly][lx - 1], sy = s_P[ly + 1][lx] + s_P[ly - 1][lx];
-        thx = SC::lam(c) * fabs(fma((S)-2, P0, sx) * recip(fma((S)2, P0, sx)));
-        thy = SC::lam(c) * fabs(fma((S)-2, P0, sy) * recip(fma((S)2, P0, sy)));
-      }
-      const S akx = fabs(from_d<S>(ux) * SC::kx(c)), aky = fabs(from_d<S>(uy) * SC::ky(c));
-      if (akx > (S)1 || aky > (S)1) bits |= H_KAPPA;
-      S snux = 0, snuy = 0;
-      if (!(g.flags & F_NO_VISC)) {
-        snux = (S)0.5 * thx * akx * ((S)1 - akx);
-        snuy = (S)0.5 * thy * aky * ((S)1 - aky);
-      }
-      const S w0base = ((S)1 - SC::r(c)) - (S)2 * (snux + snuy);
-      const long long off = (long long)(gy + NG) * g.pitch + (gx + NG);
-      const GhostOwn go = ghost_own(g, gx, gy);
-      {
-        const S* p = f + off;
-        S acc = fma(w0base, ldc<COH>(p), s_fe[node]);
-        acc = fma(snux, ldc<COH>(p + 1) + ldc<COH>(p - 1), acc);
-        acc = fma(snuy, ldc<COH>(p + g.pitch) + ldc<COH>(p - g.pitch), acc);
-        store_node<S, 0>(fn, g, gx, gy, go, acc);
-      }
-#pragma unroll
-      for (int K = 0; K < 4; ++K) {
-        S fe[8];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) fe[d] = s_fe[(1 + 8 * K + d) * NN + node];
-        ring_stencil<S, COH>(K, f, fn, g, c, off, gx, gy, go, fe, w0base, snux, snuy);
-      }
-    }
+    staged_update<S, BX, BY, RY, SW, DW, COH>(f, fn, g, c, x0, y0, s_n, s_ux, s_uy, s_T, s_P, s_fe, bits);
   } else {
   // Phase 2: Eq. 17 at the tile's interior nodes.
 #pragma unroll 1
