@@ -54,7 +54,7 @@ FP64_OPS_PER_LUP = {"fp64": 570, "fp32": 145, "fneq32": 927, "fp32dw": 19}
 # k_update), by (precision, tile variant): ncu dram__bytes_read.sum + dram__bytes_write.sum of one
 # step of this bench's 4096^2 workload (single-pass capture), divided by the sites. Reported as roofline.traffic when the autotuner
 # picks the captured variant, else null.
-TRAFFIC_B_PER_SITE = {("fp32", 2): 268.5, ("fp32", 6): 267.5, ("fp32", 11): 467.8, ("fp64", 7): 836.7,
+TRAFFIC_B_PER_SITE = {("fp32", 2): 268.5, ("fp32", 6): 267.6, ("fp32", 11): 467.8, ("fp64", 7): 836.7,
                       ("fp64", 10): 873.5, ("fp32dw", 6): 266.3, ("fp32dw", 12): 263.1}
 # Warp instructions issued per site update (ncu smsp__inst_executed over the sites, 2048^2, same
 # kernels), by (precision, tile variant): the double-word step binds on instruction issue, whose
