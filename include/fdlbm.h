@@ -242,10 +242,14 @@ int fdlbm_variant_count(void);
 int fdlbm_set_variant(fdlbm_t h, int variant);  /* FDLBM_E_ARG if out of range */
 int fdlbm_get_variant(fdlbm_t h);               /* current variant, or a negative status */
 
-/* Autotuner: time every variant with trial_steps launches on the current state and keep the
- * fastest. The state is not advanced: each trial launch reads the current buffer and writes the
- * other, which the next real step overwrites. times_ms (may be NULL) receives
- * fdlbm_variant_count() mean launch times in milliseconds. Synchronises the stream.
+/* Autotuner: time every variant over trial_steps steps on the current state and keep the
+ * fastest. The state is not advanced. On grids of up to 262144 sites every variant is timed over at
+ * least 32 steps that alternate the buffers as fdlbm_step does (steps of tens of microseconds, where
+ * launching and the persistent variants' start-up count), from a copy of the state and health word
+ * that is restored after each variant (device memory for the copy: one state buffer). On larger
+ * grids each trial launch reads the current buffer and writes the other, which the next real step
+ * overwrites. times_ms (may be NULL) receives fdlbm_variant_count() mean times per step in
+ * milliseconds. Synchronises the stream.
  * FDLBM_FP64_STRICT has one kernel pair: nothing is timed and times_ms gets zeros. */
 int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms);
 

@@ -738,12 +738,17 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
   if (e != cudaSuccess) return cuda_fail(h, e, "autotune events");
   int best = h->variant;
   float best_ms = 1e30f;
-  // The persistent variants advance the state over their trial launch: they are timed on small grids
-  // only (where they can win), from a snapshot of the current buffer and health word restored after.
-  const bool persist_ok = (h->cfg.prec == FDLBM_FP64 || h->cfg.prec == FDLBM_FP32_STORE) && !any_segment(h) &&
-                          (long long)h->cfg.nx * h->cfg.ny <= 262144;
+  // On small grids the trials advance the state, from a snapshot of the current buffer and health
+  // word restored after each variant: the persistent variants (timed there only, where they can
+  // win) over their launch, the one-step variants by alternating the buffers as fdlbm_step does.
+  const bool small = (long long)h->cfg.nx * h->cfg.ny <= 262144;
+  const bool persist_ok = (h->cfg.prec == FDLBM_FP64 || h->cfg.prec == FDLBM_FP32_STORE) && !any_segment(h) && small;
+  // Small grids step in tens of microseconds: a few trial steps would weigh the persistent launch's
+  // fixed start-up against back-to-back one-step launches, so every variant is timed over at least
+  // kSmallGridTrialSteps steps there (a few milliseconds in all).
+  const int tsteps = small && trial_steps < kSmallGridTrialSteps ? kSmallGridTrialSteps : trial_steps;
   unsigned char* snap = nullptr;
-  if (persist_ok) {
+  if (small) {
     e = cudaMalloc(&snap, h->fbytes + 256);
     if (e == cudaSuccess) e = cudaMemcpyAsync(snap, h->f[h->cur], h->fbytes, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess)
@@ -761,11 +766,11 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
       continue;
     }
     if (variant_persistent(v)) {
-      e = launch_steps_persist(h->cfg.prec, v, h->f[h->cur], h->f[1 - h->cur], trial_steps, h->grid, h->coeffs,
+      e = launch_steps_persist(h->cfg.prec, v, h->f[h->cur], h->f[1 - h->cur], tsteps, h->grid, h->coeffs,
                                h->d_health, h->d_bar, h->stream);  // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
       if (e == cudaSuccess)
-        e = launch_steps_persist(h->cfg.prec, v, h->f[h->cur], h->f[1 - h->cur], trial_steps, h->grid, h->coeffs,
+        e = launch_steps_persist(h->cfg.prec, v, h->f[h->cur], h->f[1 - h->cur], tsteps, h->grid, h->coeffs,
                                  h->d_health, h->d_bar, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
       if (e == cudaSuccess) e = cudaMemcpyAsync(h->f[h->cur], snap, h->fbytes, cudaMemcpyDeviceToDevice, h->stream);
@@ -774,7 +779,7 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
       if (e == cudaSuccess) e = cudaEventSynchronize(b);
       float ms = 0.f;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-      ms /= trial_steps;
+      ms /= tsteps;
       if (times_ms) times_ms[v] = ms;
       if (e == cudaSuccess && ms < best_ms) {
         best_ms = ms;
@@ -782,16 +787,25 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
       }
       continue;
     }
-    // warm-up launch, then the timed ones; every launch maps f[cur] -> f[1-cur]
+    // warm-up launch, then the timed ones. With the snapshot (small grids) they step like
+    // fdlbm_step, alternating the buffers, and the state is restored after: relaunching one buffer
+    // pair with the same arguments times a 400 x 4 step at 14.3 us against its 16.4 us in a long
+    // call. Without it (large grids, whose steps take milliseconds) every launch maps
+    // f[cur] -> f[1-cur] and the state is not advanced.
     e = launch_step(h->cfg.prec, v, h->f[h->cur], h->f[1 - h->cur], h->grid, h->coeffs, h->d_health, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
-    for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
-      e = launch_step(h->cfg.prec, v, h->f[h->cur], h->f[1 - h->cur], h->grid, h->coeffs, h->d_health, h->stream);
+    for (int t = 0; t < tsteps && e == cudaSuccess; ++t) {
+      const int src = snap && (t & 1) ? 1 - h->cur : h->cur;
+      e = launch_step(h->cfg.prec, v, h->f[src], h->f[1 - src], h->grid, h->coeffs, h->d_health, h->stream);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+    if (snap && e == cudaSuccess) e = cudaMemcpyAsync(h->f[h->cur], snap, h->fbytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (snap && e == cudaSuccess)
+      e = cudaMemcpyAsync(h->d_health, snap + h->fbytes, sizeof(unsigned), cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-    ms /= trial_steps;
+    ms /= tsteps;
     if (times_ms) times_ms[v] = ms;
     if (e == cudaSuccess && ms < best_ms) {
       best_ms = ms;

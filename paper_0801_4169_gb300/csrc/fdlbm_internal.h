@@ -127,6 +127,8 @@ inline bool variant_needs_mom(int v) { return v == V_S32x16 || v == V_S32x32; }
 inline bool variant_persistent(int v) { return v == V_PRP8x4 || v == V_PT32x16; }
 inline int variant_one_step(int v) { return v == V_PRP8x4 ? V_RP8x4 : v == V_PT32x16 ? V_T32x16 : v; }
 constexpr int kPersistMaxSteps = 4096;
+// fdlbm_autotune times every variant over at least this many steps on grids of up to 262144 sites.
+constexpr int kSmallGridTrialSteps = 32;
 
 // Kernel launchers (fdlbm_aux.cu, fdlbm_step_f32.cu, fdlbm_step_f64.cu, fdlbm_fneq.cu). All return
 // cudaGetLastError() of the launch. prec is enum fdlbm_prec.

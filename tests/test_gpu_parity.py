@@ -234,6 +234,22 @@ def test_autotune_keeps_state():
     assert s.steps_done == 0
 
 
+@pytest.mark.parametrize("prec", [F.FDLBM_FP64, F.FDLBM_FP32_STORE, F.FDLBM_FP32_STORE_DW, F.FDLBM_FNEQ32])
+def test_autotune_on_a_small_grid_restores_the_state(prec):
+    """On small grids the trials step from a copy of the state, alternating the buffers: the state,
+    step count and health are those before the call, in every storage precision."""
+    w = W.riemann4q(n=150, steps=10)
+    s = F.Solver.from_workload(w, prec)
+    s.step(3)
+    f0 = s.get_f()
+    times = s.autotune(3)
+    assert len(times) == F.fdlbm_variant_count() and any(t > 0 for t in times)
+    assert np.array_equal(s.get_f(), f0)
+    assert s.steps_done == 3 and s.health() == 0
+    s.step(2)  # and the solve goes on from there
+    assert s.sync() == 0
+
+
 def test_split_variants_need_a_moment_buffer():
     """Grids of up to 65 536 sites have no moment buffer: the split variants are refused and the
     autotuner reports them as not timed (0)."""
