@@ -187,7 +187,11 @@ int fdlbm_set_macro_device(fdlbm_t h, const double* rho, const double* u, const 
 /* Advance nsteps >= 0 time steps (Eq. 17), asynchronously on the stream.
  * Returns a sticky error found by an earlier step, else FDLBM_OK; numerical
  * failure inside these steps is reported by a later call (fdlbm_sync,
- * fdlbm_get_macro, or the next fdlbm_step once the device has passed it). */
+ * fdlbm_get_macro, or the next fdlbm_step once the device has passed it).
+ * Not for stream capture: each call ends by copying the health word to the host and recording
+ * an event on the stream, which the next call polls; captured into a CUDA graph, that event is
+ * not a recorded one, and the next call reports FDLBM_E_CUDA. Batches replay their steps from
+ * graphs of their own (fdlbm_batch_step). */
 int fdlbm_step(fdlbm_t h, long nsteps);
 
 /* Wait for the handle's stream and return its status (FDLBM_E_NUMERIC if a
