@@ -68,6 +68,7 @@ DTYPE = {"fp64": "f64", "fp32": "f32-store/fixed-point+f64-moments/f64-feq",
 SPLIT_VARIANTS = (10, 11)
 # Variants that run all the steps of a call in one cooperative launch (up to 4096 steps each).
 PERSISTENT_VARIANTS = (13, 14)
+GRAPH_VARIANT = 15  # the ring-parallel step launched from captured CUDA graphs
 BYTES_PER_LUP_SPLIT = {"fp64": 3 * 33 * 8 + 2 * (4 * 8 + 8), "fp32": 3 * 33 * 4 + 2 * (4 * 8 + 4),
                        "fp32dw": 3 * 33 * 4 + 2 * (4 * 8 + 4)}
 # Minimum HBM bytes per site update: read and write all 33 f once.
@@ -650,6 +651,8 @@ def main():
                      "k_moments + k_update (split step)" if split else
                      "k_step_tma (fused step, tile by tensor copy)" if variant == 12 and prec_name in ("fp32", "fp32dw")
                      else "k_persist_rp / k_persist_tile (persistent steps)" if variant in PERSISTENT_VARIANTS
+                     and prec_name in ("fp32", "fp64")
+                     else "k_step_rp (ring-parallel steps replayed from CUDA graphs of 32)" if variant == GRAPH_VARIANT
                      and prec_name in ("fp32", "fp64") else "k_step (fused step)",
                      "achieved": achieved,
                      "peak": fp64_peak, "unit": "G FP64-pipe ops/s", "frac": achieved / fp64_peak,

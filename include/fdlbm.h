@@ -241,7 +241,11 @@ int fdlbm_load(fdlbm_t h, const char* path);
  * That removes the per-step launch cost, 3% of a 1600-site step (small grids wait on the FP64 pipe
  * of their few warps, not on launches); the autotuner times them on small grids. A solve with boundary
  * segments, other precisions and fdlbm_step_noalloc run the one-step variants 9 and 2 for them. A
- * barrier wait that gives up (bounded at about 2^22 polls) sets FDLBM_HEALTH_TIMEOUT. */
+ * barrier wait that gives up (bounded at about 2^22 polls) sets FDLBM_HEALTH_TIMEOUT. Variant 15
+ * (FP64 and FP32 storage) launches variant 9's step from CUDA graphs of 32 steps, captured the
+ * first time they are needed (one per starting buffer, on a stream of the handle's own) and
+ * replayed on the handle's stream; a call's steps beyond a multiple of 32, solves with boundary
+ * segments and other precisions launch variant 9 step by step. */
 int fdlbm_variant_count(void);
 int fdlbm_set_variant(fdlbm_t h, int variant);  /* FDLBM_E_ARG if out of range */
 int fdlbm_get_variant(fdlbm_t h);               /* current variant, or a negative status */

@@ -52,7 +52,7 @@ cudaError_t launch_segment(int prec, void* f, const Grid& g, const Coeffs& c, co
 
 cudaError_t launch_step(int prec, int variant, const void* f, void* fn, const Grid& g, const Coeffs& c,
                         unsigned* health, cudaStream_t s) {
-  variant = variant_one_step(variant);  // one step of a persistent variant: its tile body
+  variant = variant_one_step(variant);  // one step of a persistent or graph-replayed variant: its tile body
   if (prec == FDLBM_FNEQ32) return launch_step_fneq(variant, f, fn, g, c, health, s);
   if (prec == FDLBM_FP64_STRICT) return launch_step_strict(f, fn, g, c, health, s);  // one kernel pair
   if (variant == V_TMA32x8) {

@@ -219,6 +219,41 @@ int enqueue_health_copy(fdlbm_ctx* h) {
 
 bool any_segment(const fdlbm_ctx* h) { return h->seg_on[0] || h->seg_on[1] || h->seg_on[2] || h->seg_on[3]; }
 
+// V_GRP8x4 applies (else its steps are launched one by one as V_RP8x4).
+bool graph_ok(const fdlbm_ctx* h) {
+  return (h->cfg.prec == FDLBM_FP64 || h->cfg.prec == FDLBM_FP32_STORE) && !any_segment(h);
+}
+
+// The executable graph of kGraphSteps ring-parallel steps starting from buffer `start`, captured on
+// the handle's private stream the first time it is needed. The launches' arguments (buffers, grid,
+// coefficients, health word) are fixed for the handle's life, so a graph stays valid until
+// fdlbm_destroy. Capture launches nothing; a replay runs on the handle's stream.
+int graph_exec(fdlbm_ctx* h, int start, cudaGraphExec_t* out) {
+  if (h->gexec[start]) {
+    *out = h->gexec[start];
+    return FDLBM_OK;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(h, e, "capture stream");
+  e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+  int c = start;
+  cudaError_t le = cudaSuccess;
+  for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k, c = 1 - c)
+    le = launch_step(h->cfg.prec, V_RP8x4, h->f[c], h->f[1 - c], h->grid, h->coeffs, h->d_health, h->cap_stream);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(h->cap_stream, &graph);  // ends the capture whatever happened inside
+  if (le != cudaSuccess) e = le;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
+  h->gexec[start] = exec;
+  *out = exec;
+  return FDLBM_OK;
+}
+
 // The Dirichlet segments of every side at the time of step `steps_at` (t = steps_at * dt), in
 // buffer buf.
 int apply_segments(fdlbm_ctx* h, void* buf, long steps_at) {
@@ -479,7 +514,18 @@ int fdlbm_step(fdlbm_t h, long nsteps) {
     if (nsteps > 0) return enqueue_health_copy(h);
     return FDLBM_OK;
   }
-  for (long s = 0; s < nsteps; ++s) {
+  long left = nsteps;
+  if (variant_graph(h->variant) && graph_ok(h)) {
+    for (; left >= kGraphSteps; left -= kGraphSteps) {
+      cudaGraphExec_t ge = nullptr;
+      const int rc = graph_exec(h, h->cur, &ge);
+      if (rc) return rc;
+      const cudaError_t e = cudaGraphLaunch(ge, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "step graph launch");
+      h->steps += kGraphSteps;  // an even count: the state is back in buffer cur
+    }
+  }
+  for (long s = 0; s < left; ++s) {
     cudaError_t e = launch_step(h->cfg.prec, h->variant, h->f[h->cur], h->f[1 - h->cur], h->grid, h->coeffs,
                                 h->d_health, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
@@ -761,8 +807,34 @@ int fdlbm_autotune(fdlbm_t h, int trial_steps, float* times_ms) {
     }
   }
   for (int v = 0; v < V_COUNT && e == cudaSuccess; ++v) {
-    if ((variant_needs_mom(v) && !h->grid.mom) || (variant_persistent(v) && !persist_ok)) {  // not available here
-      if (times_ms) times_ms[v] = 0.f;
+    if ((variant_needs_mom(v) && !h->grid.mom) || ((variant_persistent(v) || variant_graph(v)) && !persist_ok)) {
+      if (times_ms) times_ms[v] = 0.f;  // not available here
+      continue;
+    }
+    if (variant_graph(v)) {  // replays from the current buffer (each ends there), then the snapshot
+      const int replays = tsteps > kGraphSteps ? tsteps / kGraphSteps : 1;
+      cudaGraphExec_t ge = nullptr;
+      const int rc = graph_exec(h, h->cur, &ge);
+      if (rc) {
+        e = cudaErrorUnknown;
+        break;
+      }
+      e = cudaGraphLaunch(ge, h->stream);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+      for (int r = 0; r < replays && e == cudaSuccess; ++r) e = cudaGraphLaunch(ge, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->f[h->cur], snap, h->fbytes, cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_health, snap + h->fbytes, sizeof(unsigned), cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      ms /= (float)replays * kGraphSteps;
+      if (times_ms) times_ms[v] = ms;
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
       continue;
     }
     if (variant_persistent(v)) {
@@ -848,6 +920,9 @@ int fdlbm_destroy(fdlbm_t h) {
   if (h->d_fstage) cudaFree(h->d_fstage);
   if (h->h_health) cudaFreeHost(h->h_health);
   if (h->ev) cudaEventDestroy(h->ev);
+  for (int b = 0; b < 2; ++b)
+    if (h->gexec[b]) cudaGraphExecDestroy(h->gexec[b]);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return FDLBM_OK;
 }

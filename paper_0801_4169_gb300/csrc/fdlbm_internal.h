@@ -118,15 +118,22 @@ inline void variant_tile(int v, int* tw, int* th) {
 // steps of a call (up to kPersistMaxSteps), the CTAs meeting at a grid barrier between steps, with
 // the tile bodies of V_RP8x4 and V_T32x16 (fdlbm_step_persist.cu). One-step paths (the no-alloc
 // entry point, other precisions, solves with boundary segments) run those one-step variants.
+// V_GRP8x4 (FP64 and FP32 storage): the ring-parallel 8 x 4 step replayed from CUDA graphs of
+// kGraphSteps launches, captured once per starting buffer; the steps of a call beyond a multiple of
+// kGraphSteps, and every other path, launch V_RP8x4 one by one.
 enum StepVariant {
   V_T32x4 = 0, V_T32x8 = 1, V_T32x16 = 2, V_T16x4 = 3, V_T64x8 = 4, V_T32x32 = 5, V_T32x24 = 6,
   V_T32x28 = 7, V_TILE_COUNT = 8, V_RP16x4 = 8, V_RP8x4 = 9, V_S32x16 = 10, V_S32x32 = 11, V_TMA32x8 = 12,
-  V_PRP8x4 = 13, V_PT32x16 = 14, V_COUNT = 15
+  V_PRP8x4 = 13, V_PT32x16 = 14, V_GRP8x4 = 15, V_COUNT = 16
 };
 inline bool variant_needs_mom(int v) { return v == V_S32x16 || v == V_S32x32; }
 inline bool variant_persistent(int v) { return v == V_PRP8x4 || v == V_PT32x16; }
-inline int variant_one_step(int v) { return v == V_PRP8x4 ? V_RP8x4 : v == V_PT32x16 ? V_T32x16 : v; }
+inline bool variant_graph(int v) { return v == V_GRP8x4; }
+inline int variant_one_step(int v) {
+  return v == V_PRP8x4 || v == V_GRP8x4 ? V_RP8x4 : v == V_PT32x16 ? V_T32x16 : v;
+}
 constexpr int kPersistMaxSteps = 4096;
+constexpr int kGraphSteps = 32;  // launches per captured graph (even: a replay ends in its first buffer)
 // fdlbm_autotune times every variant over at least this many steps on grids of up to 262144 sites.
 constexpr int kSmallGridTrialSteps = 32;
 
@@ -241,6 +248,8 @@ struct fdlbm_ctx {
   size_t fstage_cap = 0;       // doubles
   unsigned* h_health = nullptr;  // pinned
   cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;            // private stream the step graphs are captured on
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // V_GRP8x4: kGraphSteps steps from buffer 0 / 1
   cudaEvent_t ev = nullptr;
   bool ev_pending = false;
   bool initialised = false;
